@@ -1,0 +1,132 @@
+"""CPU oracle for the parallel in-place random permutation.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product library never links, loads or calls it, and it shares no
+code with the CUDA path (see ``knuth.c`` for the arithmetic, written out from
+Section 4.1 of the paper and from the published SplitMix64 definition).
+
+The C part (``knuth.c``) is compiled with the host C compiler into
+``_liboracle.so`` next to this file; :func:`build` does that and
+:func:`lib` loads it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "knuth.c")
+_SO = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ELEM_BYTES = {"u32": 4, "u64": 8, "rec128": 16}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``knuth.c`` into ``_liboracle.so`` (plain C, -O2, no CPU-specific flags)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+            L.oracle_splitmix64.argtypes = [u64]
+            L.oracle_splitmix64.restype = u64
+            L.oracle_mulhi64.argtypes = [u64, u64]
+            L.oracle_mulhi64.restype = u64
+            L.oracle_swap_target.argtypes = [u64, u64]
+            L.oracle_swap_target.restype = u64
+            L.oracle_fill_targets.argtypes = [u64, u64, vp]
+            L.oracle_fill_targets.restype = None
+            L.oracle_knuth_hash.argtypes = [vp, u64, u32, u64]
+            L.oracle_knuth_hash.restype = ctypes.c_int
+            L.oracle_knuth_explicit.argtypes = [vp, u64, u32, vp]
+            L.oracle_knuth_explicit.restype = ctypes.c_int
+            L.oracle_perm_histogram.argtypes = [u32, u64, u64, vp]
+            L.oracle_perm_histogram.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().oracle_splitmix64(x))
+
+
+def mulhi64(a: int, b: int) -> int:
+    return int(lib().oracle_mulhi64(a, b))
+
+
+def swap_target(seed: int, i: int) -> int:
+    """H[i] for the hashed generator (0-based, in [0, i])."""
+    return int(lib().oracle_swap_target(seed, i))
+
+
+def swap_targets(seed: int, n: int) -> np.ndarray:
+    """H[0..n) as uint64 (H[0] == 0)."""
+    out = np.empty(n, dtype=np.uint64)
+    if n:
+        lib().oracle_fill_targets(seed, n, out.ctypes.data)
+    return out
+
+
+def _elem_bytes(arr: np.ndarray) -> int:
+    if arr.ndim == 1:
+        return arr.dtype.itemsize
+    if arr.ndim == 2:
+        return arr.dtype.itemsize * arr.shape[1]
+    raise ValueError("array must be 1-D (scalar elements) or 2-D (records)")
+
+
+def knuth_hash(arr: np.ndarray, seed: int) -> np.ndarray:
+    """Sequential Knuth shuffle of ``arr`` in place with hashed targets.
+
+    ``arr`` is 1-D of 4- or 8-byte scalars, or 2-D (n, w) whose rows are
+    16-byte records.  Returns ``arr``.
+    """
+    assert arr.flags["C_CONTIGUOUS"]
+    eb = _elem_bytes(arr)
+    rc = lib().oracle_knuth_hash(arr.ctypes.data, arr.shape[0], eb, seed)
+    if rc != 0:
+        raise ValueError(f"oracle_knuth_hash failed ({rc}); element size {eb}")
+    return arr
+
+
+def knuth_explicit(arr: np.ndarray, H) -> np.ndarray:
+    """Sequential Knuth shuffle of ``arr`` in place with explicit targets ``H``."""
+    assert arr.flags["C_CONTIGUOUS"]
+    h = np.ascontiguousarray(H, dtype=np.uint32)
+    if h.shape[0] != arr.shape[0]:
+        raise ValueError("H must have one entry per element")
+    eb = _elem_bytes(arr)
+    rc = lib().oracle_knuth_explicit(arr.ctypes.data, arr.shape[0], eb, h.ctypes.data)
+    if rc == -2:
+        raise ValueError("H[i] > i for some i")
+    if rc != 0:
+        raise ValueError(f"oracle_knuth_explicit failed ({rc})")
+    return arr
+
+
+def perm_histogram(n: int, count: int, seed_stride: int) -> np.ndarray:
+    """Counts of each of the n! output permutations of [0..n) over ``count`` seeds."""
+    import math
+
+    counts = np.zeros(math.factorial(n), dtype=np.uint64)
+    rc = lib().oracle_perm_histogram(n, count, seed_stride, counts.ctypes.data)
+    if rc != 0:
+        raise ValueError("n must be in [1, 10]")
+    return counts

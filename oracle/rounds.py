@@ -1,0 +1,86 @@
+"""Round-by-round simulator of the parallel Knuth shuffle (debugging aid).
+
+TEST INFRASTRUCTURE ONLY (same rule as the rest of ``oracle/``).
+
+This is a plain restatement of Algorithm 1 (Section 4.1) run under the
+deterministic-reservations framework of Section 7.2 / Appendix A.1: each round
+works on the first ``k`` unfinished swaps in sequential order (the Decomposable
+Property's prefix of n^(1-eps) swaps, Section 4.1), every one of them reserves,
+then the ones whose reservations all hold commit, and the rest are packed and
+retried.  Two reservation rules are offered:
+
+* ``"two"`` -- Algorithm 1 as printed: swap s writes max(R[s], s) and
+  max(R[H[s]], s); it commits when R[s] = s and R[H[s]] = s.
+* ``"oneres"`` -- the RP-OneRes rule of Appendix A.2: only R[H[s]] is written;
+  swap s commits when (R[s] is unset or R[s] = s) and R[H[s]] = s.
+
+Self-loops (H[s] = s) are removed, as the text under Algorithm 1 says, when
+``skip_self_loops`` is true: they never reserve and finish in their first
+round.  Indices are 0-based: the paper's step p is step p-1 here, and a larger
+index is an earlier sequential step, so ``max`` picks the earliest.
+
+The per-round winner sets are returned so that tests can compare them with the
+worked example of Figure 3.  The final array is also returned; it equals the
+sequential Knuth shuffle whenever the rule is correct, which is what makes this
+a useful cross-check of ``knuth.c`` (and vice versa).  Round counts are not a
+parity target for the GPU path (its prefix, rule variant and self-loop handling
+may differ).
+"""
+from __future__ import annotations
+
+
+def simulate(A, H, k: int | None = None, rule: str = "oneres", skip_self_loops: bool = True):
+    """Run the round simulator.
+
+    A: list of elements (copied, not modified); H: list of 0-based targets with
+    H[i] <= i; k: prefix size (None = all unfinished swaps each round).
+    Returns (final list, list of per-round winner sets).
+    """
+    n = len(A)
+    if len(H) != n:
+        raise ValueError("H must have one entry per element")
+    for i in range(1, n):
+        if not (0 <= H[i] <= i):
+            raise ValueError(f"H[{i}]={H[i]} is outside [0, {i}]")
+    if rule not in ("two", "oneres"):
+        raise ValueError("rule must be 'two' or 'oneres'")
+    A = list(A)
+    unfinished = list(range(n - 1, 0, -1))  # sequential order: n-1 first; step 0 is a no-op
+    rounds = []
+    while unfinished:
+        prefix = unfinished if k is None else unfinished[:k]
+        rest = [] if k is None else unfinished[k:]
+        R = {}  # reservation map: location -> max step index written there
+
+        def reserve(loc, s):
+            R[loc] = max(R.get(loc, -1), s)
+
+        # reserve phase
+        for s in prefix:
+            if skip_self_loops and H[s] == s:
+                continue
+            if rule == "two":
+                reserve(s, s)
+            reserve(H[s], s)
+        # commit phase: decide every swap against the full R, then apply
+        winners = []
+        for s in prefix:
+            if skip_self_loops and H[s] == s:
+                winners.append(s)
+                continue
+            own = R.get(s, -1)
+            if rule == "two":
+                ok = own == s and R.get(H[s], -1) == s
+            else:
+                ok = (own == -1 or own == s) and R.get(H[s], -1) == s
+            if ok:
+                winners.append(s)
+        won = set(winners)
+        # the committed swaps touch disjoint locations, so any order gives the same array
+        for s in winners:
+            t = H[s]
+            A[s], A[t] = A[t], A[s]
+        rounds.append(won)
+        # pack the leftovers, keeping sequential order, ahead of the untouched rest
+        unfinished = [s for s in prefix if s not in won] + rest
+    return A, rounds

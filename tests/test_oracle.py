@@ -1,0 +1,234 @@
+"""Pins for the CPU oracle (runs without a GPU).
+
+Each test checks the oracle against something other than itself: the paper's
+worked example (Figure 3), published SplitMix64 output, closed forms of the
+Knuth shuffle for special target sequences, the bijection between target
+sequences and permutations (brute force over every H for n <= 7), the
+permutation invariant, and a chi-square test of uniformity.
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rounds
+from tests.conftest import read_golden
+
+M64 = (1 << 64) - 1
+
+
+# ---------------------------------------------------------------- hash pins
+def test_splitmix64_published_vectors():
+    g = read_golden("splitmix64_published.txt")
+    state = int(g["seed"])
+    for expected in map(int, g["outputs"].split()):
+        # the generator's call t mixes (seed + t * gamma); the oracle's function
+        # takes the pre-increment state
+        assert oracle.splitmix64(state) == expected
+        state = (state + 0x9E3779B97F4A7C15) & M64
+    assert oracle.splitmix64(0) == int(g["zero_state_first_output"], 16)
+
+
+def test_mulhi64_is_floor_of_product_over_2_64():
+    rng = random.Random(12345)
+    cases = [(0, 0), (M64, M64), (M64, 1), (1 << 63, 2), (M64, 1 << 32)]
+    cases += [(rng.getrandbits(64), rng.getrandbits(64)) for _ in range(2000)]
+    for a, b in cases:
+        assert oracle.mulhi64(a, b) == (a * b) >> 64
+
+
+def test_swap_target_range_and_composition():
+    g = read_golden("splitmix64_published.txt")
+    # composition H[i] = floor(splitmix64(seed ^ i) * (i + 1) / 2^64), spot-checked
+    # on the published vector's state so both factors are pinned externally
+    state = int(g["seed"])
+    first = int(g["outputs"].split()[0])
+    for i in (0, 1, 7, 1000):
+        seed = state ^ i
+        assert oracle.swap_target(seed, i) == (first * (i + 1)) >> 64
+    for seed in (0, 1, 2, 3, 0xDEADBEEF):
+        H = oracle.swap_targets(seed, 5000)
+        assert H[0] == 0
+        idx = np.arange(5000, dtype=np.uint64)
+        assert np.all(H <= idx)
+
+
+def test_swap_target_is_roughly_uniform_on_0_i():
+    # H[i] / (i + 1) should be uniform on [0, 1): check the mean and the
+    # fraction in the lower half over many i (a dropped +1 or a shift would bias it)
+    H = oracle.swap_targets(99, 200000).astype(np.float64)
+    i = np.arange(200000, dtype=np.float64)
+    u = (H[1000:] + 0.5) / (i[1000:] + 1)
+    assert abs(u.mean() - 0.5) < 0.005
+    assert abs((u < 0.5).mean() - 0.5) < 0.005
+    # the top value i itself is reachable: H[i] == i happens about ln(n) times
+    assert np.sum(H[1:] == i[1:]) >= 3
+
+
+# ---------------------------------------------------------------- Figure 3
+def test_figure3_worked_example():
+    g = read_golden("fig3_worked_example.txt")
+    h1 = [int(x) for x in g["h_one_based"].split()]
+    h0 = [int(x) for x in g["h_zero_based"].split()]
+    assert h0 == [x - 1 for x in h1]
+    expected = [int(x) for x in g["expected_output_zero_based"].split()]
+    for dt in (np.uint32, np.uint64):
+        A = np.arange(8, dtype=dt)
+        oracle.knuth_explicit(A, h0)
+        assert A.tolist() == expected
+
+
+def test_figure3_first_round_matches_printed_pairs():
+    g = read_golden("fig3_worked_example.txt")
+    h0 = [int(x) for x in g["h_zero_based"].split()]
+    printed = set()
+    for pair in g["first_round_pairs_one_based"].split():
+        a, b = (int(x) - 1 for x in pair.split("-"))
+        assert h0[a] == b  # each printed pair is (step, its target)
+        printed.add(a)
+    assert printed == {int(x) for x in g["first_round_steps_zero_based"].split()}
+    for rule in ("two", "oneres"):
+        out, rds = rounds.simulate(list(range(8)), h0, k=None, rule=rule, skip_self_loops=True)
+        assert rds[0] - {3} == printed or rds[0] == printed  # self-loop 3 may finish in round 1
+        # self-loops excluded, the printed three are exactly the first commits
+        assert {s for s in rds[0] if h0[s] != s} == printed
+        assert out == [int(x) for x in g["expected_output_zero_based"].split()]
+
+
+# ---------------------------------------------------------------- bijection
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7])
+def test_bruteforce_every_target_sequence_gives_a_distinct_permutation(n):
+    seen = set()
+    ranges = [range(i + 1) for i in range(n)]
+    import itertools
+
+    for H in itertools.product(*ranges):
+        A = np.arange(n, dtype=np.uint32)
+        oracle.knuth_explicit(A, H)
+        t = tuple(A.tolist())
+        assert sorted(t) == list(range(n))
+        seen.add(t)
+    assert len(seen) == math.factorial(n)
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("n", [2, 3, 10, 97, 1000])
+def test_closed_forms(n):
+    base = np.arange(n, dtype=np.uint64)
+    # H == 0: every step swaps with location 0 -> left rotation by one
+    A = base.copy()
+    oracle.knuth_explicit(A, np.zeros(n, dtype=np.uint32))
+    assert A.tolist() == [(i + 1) % n for i in range(n)]
+    # H[i] = i - 1: adjacent swaps downward -> right rotation by one
+    A = base.copy()
+    H = np.maximum(np.arange(n, dtype=np.int64) - 1, 0).astype(np.uint32)
+    oracle.knuth_explicit(A, H)
+    assert A.tolist() == [n - 1] + list(range(n - 1))
+    # H[i] = i: identity
+    A = base.copy()
+    oracle.knuth_explicit(A, np.arange(n, dtype=np.uint32))
+    assert A.tolist() == list(range(n))
+
+
+@pytest.mark.parametrize("n", [2, 5, 64, 1001])
+def test_sattolo_targets_give_a_single_cycle(n):
+    rng = np.random.default_rng(n)
+    H = np.zeros(n, dtype=np.uint32)
+    for i in range(1, n):
+        H[i] = rng.integers(0, i)  # strictly below i
+    A = np.arange(n, dtype=np.uint64)
+    oracle.knuth_explicit(A, H)
+    # follow the permutation from 0; a single n-cycle returns after exactly n steps
+    j, steps = 0, 0
+    while True:
+        j = int(A[j])
+        steps += 1
+        if j == 0:
+            break
+    assert steps == n
+
+
+def test_explicit_rejects_out_of_range_target():
+    A = np.arange(4, dtype=np.uint32)
+    with pytest.raises(ValueError):
+        oracle.knuth_explicit(A, [0, 0, 3, 1])
+    assert A.tolist() == [0, 1, 2, 3]  # nothing moved
+
+
+# ---------------------------------------------------------------- elements
+def test_records_move_whole_and_match_explicit_path():
+    n, seed = 4097, 3
+    H = oracle.swap_targets(seed, n)
+    keys = np.arange(n, dtype=np.uint64)
+    rec = np.stack([keys, keys * np.uint64(7) + np.uint64(1)], axis=1)
+    a = rec.copy()
+    oracle.knuth_hash(a, seed)
+    b = rec.copy()
+    oracle.knuth_explicit(b, H.astype(np.uint32))
+    assert np.array_equal(a, b)
+    assert np.array_equal(a[:, 1], a[:, 0] * np.uint64(7) + np.uint64(1))
+    # scalars of every width follow the same permutation as the records' keys
+    for dt in (np.uint32, np.uint64):
+        s = np.arange(n, dtype=dt)
+        oracle.knuth_hash(s, seed)
+        assert np.array_equal(s.astype(np.uint64), a[:, 0])
+
+
+def test_hashed_output_is_a_permutation():
+    n = 1 << 17
+    A = np.arange(n, dtype=np.uint64)
+    oracle.knuth_hash(A, 2)
+    assert np.array_equal(np.sort(A), np.arange(n, dtype=np.uint64))
+    assert not np.array_equal(A, np.arange(n, dtype=np.uint64))
+
+
+def test_degenerate_sizes():
+    for n in (0, 1):
+        A = np.arange(n, dtype=np.uint64)
+        oracle.knuth_hash(A, 5)
+        assert A.tolist() == list(range(n))
+    A = np.arange(2, dtype=np.uint64)
+    oracle.knuth_hash(A, 1)
+    # n = 2: the one real step swaps iff H[1] == 0
+    assert A.tolist() == ([1, 0] if oracle.swap_target(1, 1) == 0 else [0, 1])
+
+
+# ---------------------------------------------------------------- uniformity
+def test_chi_square_uniformity_n5():
+    """Chi-square over 1.2e6 seeds s_t = t << 8 at n = 5 (120 cells, df = 119)."""
+    from scipy import stats
+
+    count = 1_200_000
+    counts = oracle.perm_histogram(5, count, 1 << 8).astype(np.float64)
+    assert counts.sum() == count
+    expected = count / 120.0
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    p = float(stats.chi2.sf(chi2, 119))
+    assert p > 1e-3, (chi2, p)
+    assert counts.min() > 0
+
+
+# ---------------------------------------------------------------- round simulator
+@pytest.mark.parametrize("rule", ["two", "oneres"])
+@pytest.mark.parametrize("k", [None, 1, 3, 16])
+def test_round_simulator_agrees_with_sequential(rule, k):
+    rng = random.Random(7)
+    for n in (1, 2, 5, 17, 200):
+        for _ in range(5):
+            H = [0] + [rng.randint(0, i) for i in range(1, n)]
+            out, rds = rounds.simulate(list(range(n)), H, k=k, rule=rule)
+            A = np.arange(n, dtype=np.uint64)
+            oracle.knuth_explicit(A, H)
+            assert out == A.tolist()
+            # every round commits at least the highest unfinished step
+            assert all(len(r) >= 1 for r in rds)
+
+
+def test_round_simulator_chain_has_one_winner_per_round():
+    n = 64
+    H = [0] * n  # every step targets location 0: a dependence chain of depth n-1
+    out, rds = rounds.simulate(list(range(n)), H, k=None, rule="oneres")
+    assert len(rds) == n - 1 and all(len(r) == 1 for r in rds)
+    assert out == [(i + 1) % n for i in range(n)]

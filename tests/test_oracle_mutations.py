@@ -1,0 +1,125 @@
+"""The oracle's pins catch plausible mistakes (runs without a GPU).
+
+Each case plants one mistake in a temporary copy of ``oracle/knuth.c`` (a
+dropped term, a wrong constant, index or operand, a reversed loop), compiles
+it, and checks that at least one of the pins used in ``test_oracle.py`` fails
+on the mutant.  The real oracle passes the same pins.
+"""
+import ctypes
+import itertools
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from tests.conftest import ROOT, read_golden
+
+SRC = os.path.join(ROOT, "oracle", "knuth.c")
+
+MUTATIONS = {
+    "loop_runs_upward": ("for (uint64_t i = n; i-- > 1;)\n        swap_elems(a, i, H[i], elem_bytes);",
+                         "for (uint64_t i = 1; i < n; ++i)\n        swap_elems(a, i, H[i], elem_bytes);"),
+    "hash_loop_runs_upward": ("for (uint64_t i = n; i-- > 1;) {\n        uint64_t j",
+                              "for (uint64_t i = 1; i < n; ++i) {\n        uint64_t j"),
+    "range_drops_plus_one": ("oracle_mulhi64(oracle_splitmix64(seed ^ i), i + 1)",
+                             "oracle_mulhi64(oracle_splitmix64(seed ^ i), i)"),
+    "seed_added_not_xored": ("oracle_splitmix64(seed ^ i)", "oracle_splitmix64(seed + i)"),
+    "wrong_shift": ("(z ^ (z >> 30))", "(z ^ (z >> 31))"),
+    "dropped_final_xorshift": ("return z ^ (z >> 31);", "return z;"),
+    "wrong_multiplier": ("0x94D049BB133111EBull", "0x94D049BB133111EDull"),
+    "swap_loses_write": ("memcpy(A + b * eb, tmp, eb);", ""),
+    "swap_wrong_operand": ("swap_elems(a, i, H[i], elem_bytes);", "swap_elems(a, i, H[i] / 2, elem_bytes);"),
+    "mulhi_takes_low_half": ("return (uint64_t)(p >> 64);", "return (uint64_t)(p >> 63);"),
+    "skips_last_step": ("for (uint64_t i = n; i-- > 1;)\n        swap_elems",
+                        "for (uint64_t i = n - 1; i-- > 1;)\n        swap_elems"),
+}
+
+
+def _compile(src_text, path):
+    c = path + ".c"
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", path, c])
+    L = ctypes.CDLL(path)
+    u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+    L.oracle_splitmix64.argtypes = [u64]
+    L.oracle_splitmix64.restype = u64
+    L.oracle_mulhi64.argtypes = [u64, u64]
+    L.oracle_mulhi64.restype = u64
+    L.oracle_swap_target.argtypes = [u64, u64]
+    L.oracle_swap_target.restype = u64
+    L.oracle_knuth_explicit.argtypes = [vp, u64, u32, vp]
+    L.oracle_knuth_hash.argtypes = [vp, u64, u32, u64]
+    return L
+
+
+def _pins_pass(L):
+    """The pins of test_oracle.py in compact form; True when all hold."""
+    g = read_golden("splitmix64_published.txt")
+    state = int(g["seed"])
+    for expected in map(int, g["outputs"].split()):
+        if L.oracle_splitmix64(state) != expected:
+            return False
+        state = (state + 0x9E3779B97F4A7C15) & ((1 << 64) - 1)
+    for a, b in [(2**64 - 1, 2**64 - 1), (12345678901234567, 98765432109876543)]:
+        if L.oracle_mulhi64(a, b) != (a * b) >> 64:
+            return False
+    first = int(g["outputs"].split()[0])
+    for i in (1, 7, 1000):
+        if L.oracle_swap_target(int(g["seed"]) ^ i, i) != (first * (i + 1)) >> 64:
+            return False
+    f3 = read_golden("fig3_worked_example.txt")
+    h0 = np.array([int(x) for x in f3["h_zero_based"].split()], dtype=np.uint32)
+    A = np.arange(8, dtype=np.uint64)
+    L.oracle_knuth_explicit(A.ctypes.data, 8, 8, h0.ctypes.data)
+    if A.tolist() != [int(x) for x in f3["expected_output_zero_based"].split()]:
+        return False
+    for n in (4, 5):
+        seen = set()
+        for H in itertools.product(*[range(i + 1) for i in range(n)]):
+            h = np.array(H, dtype=np.uint32)
+            A = np.arange(n, dtype=np.uint32)
+            L.oracle_knuth_explicit(A.ctypes.data, n, 4, h.ctypes.data)
+            seen.add(tuple(A.tolist()))
+        if len(seen) != math.factorial(n):
+            return False
+    n = 50
+    A = np.arange(n, dtype=np.uint64)
+    L.oracle_knuth_explicit(A.ctypes.data, n, 8, np.zeros(n, dtype=np.uint32).ctypes.data)
+    if A.tolist() != [(i + 1) % n for i in range(n)]:
+        return False
+    # hashed path: a permutation, and the same one the explicit path gives
+    n = 3000
+    H = np.array([L.oracle_swap_target(2, i) for i in range(n)], dtype=np.uint64)
+    if np.any(H > np.arange(n, dtype=np.uint64)):
+        return False
+    a = np.arange(n, dtype=np.uint64)
+    L.oracle_knuth_hash(a.ctypes.data, n, 8, 2)
+    b = np.arange(n, dtype=np.uint64)
+    L.oracle_knuth_explicit(b.ctypes.data, n, 8, H.astype(np.uint32).ctypes.data)
+    if not np.array_equal(a, b) or not np.array_equal(np.sort(a), np.arange(n, dtype=np.uint64)):
+        return False
+    # uniformity of H[i]/(i+1): the mean of the normalised target is 1/2
+    Hs = np.array([L.oracle_swap_target(99, i) for i in range(1000, 40000)], dtype=np.float64)
+    u = (Hs + 0.5) / (np.arange(1000, 40000) + 1.0)
+    if abs(u.mean() - 0.5) > 0.01:
+        return False
+    return True
+
+
+def test_real_oracle_passes_compact_pins(tmp_path):
+    with open(SRC) as f:
+        L = _compile(f.read(), str(tmp_path / "real.so"))
+    assert _pins_pass(L)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    with open(SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    L = _compile(text.replace(old, new), str(tmp_path / f"{name}.so"))
+    assert not _pins_pass(L), f"pins did not catch mutation {name}"
