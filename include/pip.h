@@ -1,0 +1,174 @@
+/*
+ * pip.h -- C ABI of the GB300 parallel in-place random permutation library.
+ *
+ * The library permutes an array A of n elements in place on one GPU and
+ * produces exactly the result of the sequential Knuth shuffle (Section 4.1):
+ *
+ *     for i = n-1 down to 1:  swap(A[i], A[H[i]]),   0 <= H[i] <= i
+ *
+ * (0-based; the paper is 1-based, its step p is step p-1 here, and step 0 is a
+ * no-op).  Swap targets are either hashed,
+ *
+ *     H[i] = mulhi64(splitmix64(seed XOR i), i + 1)
+ *
+ * (splitmix64 = one SplitMix64 output step from state x; mulhi64 = high 64 bits
+ * of the 128-bit product), or supplied explicitly.  The work runs as rounds of
+ * deterministic reservations (Algorithm 1, Section 7.2, Appendix A.1) over a
+ * prefix of about C * n^(1-eps) unfinished swaps, so that the auxiliary device
+ * memory is O(n^(1-eps)) (the relaxed PIP model, Section 3.2; Theorem 4.2).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers (cudaMalloc'd or any memory the
+ *    GPU can address); the caller owns them and must keep them alive until the
+ *    work queued on `stream` has finished.  Other pointers are host pointers.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls are asynchronous with respect to the host unless stated.
+ *  - Every function returns a pip_status.  No C++ exception crosses the ABI.
+ *    Argument errors are detected before anything is queued.  Errors detected
+ *    on the device (a barrier wait that ran out, an invalid explicit target)
+ *    are latched in a per-device word and reported by pip_check().
+ *  - The library keeps no state between calls other than that per-device
+ *    error word and the per-device launch attributes it caches; it is safe to
+ *    call from several host threads on different streams.
+ */
+#ifndef PIP_H
+#define PIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element type.  Elements are opaque and move whole. */
+typedef enum {
+    PIP_U32 = 0,    /* 4-byte elements,  A 4-byte aligned  */
+    PIP_U64 = 1,    /* 8-byte elements,  A 8-byte aligned  */
+    PIP_REC128 = 2  /* 16-byte records,  A 16-byte aligned */
+} pip_dtype;
+
+typedef enum {
+    PIP_OK = 0,
+    PIP_EINVAL = 1,    /* bad argument (null pointer, eps outside (0,1), n >= 2^32, misaligned A, H[i] > i) */
+    PIP_ENOMEM = 2,    /* device or host allocation failed */
+    PIP_ECUDA = 3,     /* a CUDA runtime call failed */
+    PIP_ETIMEOUT = 4,  /* a bounded device-side wait ran out; the array content is unspecified */
+    PIP_EAGAIN = 5,    /* serve poll: the request has not finished yet */
+    PIP_EBUSY = 6,     /* serve: the request is queued behind the memory budget */
+    PIP_EINTERNAL = 7  /* a device-side consistency check failed (round cap exceeded) */
+} pip_status;
+
+/* Planned execution of one shuffle (filled by pip_plan). */
+typedef struct {
+    uint64_t n;
+    uint32_t elem_bytes;
+    double eps;
+    uint32_t fresh_per_round;  /* F: fresh swaps added to the prefix each round, ~C*n^(1-eps) */
+    uint32_t max_active;       /* k: cap on the swaps active in one round (F plus carried losers) */
+    uint32_t slots;            /* reservation slots per round table */
+    uint32_t grid_blocks;      /* persistent blocks launched (0 = decided at launch) */
+    uint32_t block_threads;
+    uint64_t aux_bytes;        /* exact device scratch bytes this plan allocates */
+    uint64_t aux_bound_bytes;  /* c*n^(1-eps) + 4096 with c = PIP_AUX_C: the bound aux_bytes obeys */
+    uint64_t min_rounds;       /* ceil((n-1)/F): a lower bound on the rounds */
+} pip_plan_info;
+
+/* Aux constant c (bytes per unit of n^(1-eps)) that every plan obeys. */
+#define PIP_AUX_C 128.0
+
+/* Tuning overrides; zero fields keep the planner's choice. */
+typedef struct {
+    double prefix_c;           /* C in F = C * n^(1-eps) (clamped so aux stays within the bound) */
+    uint32_t fresh_per_round;  /* explicit F (overrides prefix_c; still clamped by the bound) */
+    uint32_t slot_factor;      /* reservation slots per active swap (2..16, default 4) */
+    uint32_t grid_blocks;      /* persistent blocks (clamped to what can be co-resident) */
+    uint32_t block_threads;    /* 128..1024, multiple of 32 */
+    uint64_t wait_timeout_ns;  /* limit of each device-side barrier wait (default 2e9 ns) */
+    uint32_t flags;            /* PIP_FLAG_* */
+} pip_options;
+
+/* Test hook: block 0 never arrives at its first barrier, so every other block's
+ * bounded wait runs out and the call reports PIP_ETIMEOUT.  The array is left
+ * untouched (the hook fires before any swap). */
+#define PIP_FLAG_TEST_SKIP_BARRIER 1u
+
+/* Per-call statistics written by the device at the end of a shuffle. */
+typedef struct {
+    uint32_t status;          /* pip_status of the device-side run */
+    uint32_t rounds;          /* rounds executed */
+    uint64_t attempts;        /* sum over rounds of the active swaps (F per round plus losers) */
+    uint64_t losers;          /* sum over rounds of the swaps carried to the next round */
+    uint32_t max_active;      /* largest active set seen */
+    uint32_t grid_blocks;     /* blocks that ran */
+    uint64_t reserved[4];
+} pip_stats;
+
+/*
+ * pip_shuffle -- in-place Knuth shuffle of A_dev[0..n) with hashed targets
+ * H[i] = mulhi64(splitmix64(seed ^ i), i + 1) (Section 4.1, Theorem 4.2).
+ *   A_dev : device array of n elements of `dtype`, aligned to the element size.
+ *   n     : element count, n < 2^32.  n <= 1 is a no-op returning PIP_OK.
+ *   eps   : 0 < eps < 1; the prefix is about n^(1-eps) swaps, the device
+ *           scratch at most pip_aux_bytes(n, dtype, eps) bytes.
+ *   stream: cudaStream_t (void*), NULL = default stream.
+ * Allocates its scratch with cudaMallocAsync on `stream` and frees it the same
+ * way.  Deterministic: equal arguments give equal output.
+ */
+pip_status pip_shuffle(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed,
+                       double eps, void *stream);
+
+/*
+ * pip_shuffle_explicit_h -- the same with caller-supplied targets
+ * H_dev[0..n) (uint32, device, H_dev[0] ignored, 0 <= H_dev[i] <= i).  The
+ * targets are validated on the device first; a violation leaves A untouched
+ * and is reported as PIP_EINVAL by pip_check().  Used by the tests to drive
+ * the kernels through every target sequence of small n and through the
+ * closed-form worst cases (H = 0, H[i] = i-1).
+ */
+pip_status pip_shuffle_explicit_h(void *A_dev, uint64_t n, pip_dtype dtype,
+                                  const uint32_t *H_dev, double eps, void *stream);
+
+/*
+ * pip_shuffle_ex -- full-control form of the two calls above.
+ *   H_dev    : NULL for hashed targets (seed used), else explicit targets.
+ *   opt      : host pointer to overrides, or NULL.
+ *   aux_dev  : caller-provided device scratch of aux_bytes bytes (at least the
+ *              plan's aux_bytes, 256-byte aligned), or NULL to allocate.
+ *   stats_dev: device pointer to a pip_stats the kernel fills, or NULL.
+ */
+pip_status pip_shuffle_ex(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed,
+                          const uint32_t *H_dev, double eps, const pip_options *opt,
+                          void *aux_dev, uint64_t aux_bytes, pip_stats *stats_dev,
+                          void *stream);
+
+/*
+ * pip_plan -- the plan pip_shuffle_ex would use for these arguments on the
+ * current device (host only; queries device attributes, launches nothing).
+ *   out : host pointer, filled on PIP_OK.
+ */
+pip_status pip_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options *opt,
+                    pip_plan_info *out);
+
+/* pip_aux_bytes -- exact device scratch bytes pip_shuffle allocates for these
+ * arguments with default options; 0 when n <= 1 or the arguments are invalid. */
+uint64_t pip_aux_bytes(uint64_t n, pip_dtype dtype, double eps);
+
+/*
+ * pip_check -- synchronizes `stream`, then returns and clears the error latched
+ * by device-side work on the current device (PIP_OK if none), or PIP_ECUDA if
+ * the stream reported a CUDA error.
+ */
+pip_status pip_check(void *stream);
+
+/* pip_status_string -- static English description of a status code. */
+const char *pip_status_string(pip_status s);
+
+/* pip_version -- library version string. */
+const char *pip_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIP_H */

@@ -1,0 +1,230 @@
+"""GB300 parallel in-place random permutation: Python binding of ``libpip_gb300.so``.
+
+This module only marshals arguments into the C ABI declared in
+``include/pip.h``; every step of the shuffle runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library has not been built, or no
+GPU is present, the calls raise.
+
+Typical use with PyTorch device memory::
+
+    import torch, paper_2103_01216_gb300 as pip
+    A = torch.arange(1 << 20, dtype=torch.int64, device="cuda")
+    pip.shuffle(A, seed=1, eps=0.5)   # queued on the current stream
+    pip.check()                       # synchronize and surface device-side errors
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpip_gb300.so")
+
+U32, U64, REC128 = 0, 1, 2
+DTYPES = {"u32": U32, "u64": U64, "rec128": REC128}
+ELEM_BYTES = {U32: 4, U64: 8, REC128: 16}
+
+STATUS = {
+    0: "PIP_OK",
+    1: "PIP_EINVAL",
+    2: "PIP_ENOMEM",
+    3: "PIP_ECUDA",
+    4: "PIP_ETIMEOUT",
+    5: "PIP_EAGAIN",
+    6: "PIP_EBUSY",
+    7: "PIP_EINTERNAL",
+}
+PIP_OK, PIP_EINVAL, PIP_ENOMEM, PIP_ECUDA, PIP_ETIMEOUT, PIP_EAGAIN, PIP_EBUSY, PIP_EINTERNAL = range(8)
+FLAG_TEST_SKIP_BARRIER = 1
+AUX_C = 128.0
+
+
+class PipError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("elem_bytes", ctypes.c_uint32),
+        ("eps", ctypes.c_double),
+        ("fresh_per_round", ctypes.c_uint32),
+        ("max_active", ctypes.c_uint32),
+        ("slots", ctypes.c_uint32),
+        ("grid_blocks", ctypes.c_uint32),
+        ("block_threads", ctypes.c_uint32),
+        ("aux_bytes", ctypes.c_uint64),
+        ("aux_bound_bytes", ctypes.c_uint64),
+        ("min_rounds", ctypes.c_uint64),
+    ]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("prefix_c", ctypes.c_double),
+        ("fresh_per_round", ctypes.c_uint32),
+        ("slot_factor", ctypes.c_uint32),
+        ("grid_blocks", ctypes.c_uint32),
+        ("block_threads", ctypes.c_uint32),
+        ("wait_timeout_ns", ctypes.c_uint64),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_uint32),
+        ("rounds", ctypes.c_uint32),
+        ("attempts", ctypes.c_uint64),
+        ("losers", ctypes.c_uint64),
+        ("max_active", ctypes.c_uint32),
+        ("grid_blocks", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint64 * 4),
+    ]
+
+
+STATS_BYTES = ctypes.sizeof(Stats)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libpip_gb300.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2103_01216_gb300._build` "
+                "(or __graft_entry__.build()); there is no CPU fallback"
+            )
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, u32, i32, dbl = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_double
+        L.pip_shuffle.argtypes = [vp, u64, i32, u64, dbl, vp]
+        L.pip_shuffle.restype = i32
+        L.pip_shuffle_explicit_h.argtypes = [vp, u64, i32, vp, dbl, vp]
+        L.pip_shuffle_explicit_h.restype = i32
+        L.pip_shuffle_ex.argtypes = [vp, u64, i32, u64, vp, dbl, ctypes.POINTER(Options), vp, u64, vp, vp]
+        L.pip_shuffle_ex.restype = i32
+        L.pip_plan.argtypes = [u64, i32, dbl, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
+        L.pip_plan.restype = i32
+        L.pip_aux_bytes.argtypes = [u64, i32, dbl]
+        L.pip_aux_bytes.restype = u64
+        L.pip_check.argtypes = [vp]
+        L.pip_check.restype = i32
+        L.pip_status_string.argtypes = [i32]
+        L.pip_status_string.restype = ctypes.c_char_p
+        L.pip_version.argtypes = []
+        L.pip_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _raise(code: int, where: str):
+    if code != PIP_OK:
+        raise PipError(code, where)
+
+
+def make_options(**kw) -> Options | None:
+    if not kw:
+        return None
+    o = Options()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _opt_ptr(o: Options | None):
+    return ctypes.byref(o) if o is not None else None
+
+
+def plan(n: int, dtype: int | str, eps: float, **options) -> dict:
+    """The plan the library would use (host only)."""
+    d = DTYPES[dtype] if isinstance(dtype, str) else dtype
+    info = PlanInfo()
+    o = make_options(**options)
+    _raise(lib().pip_plan(n, d, eps, _opt_ptr(o), ctypes.byref(info)), "pip_plan")
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+
+def aux_bytes(n: int, dtype: int | str, eps: float) -> int:
+    d = DTYPES[dtype] if isinstance(dtype, str) else dtype
+    return int(lib().pip_aux_bytes(n, d, eps))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def tensor_dtype(A) -> int:
+    """pip dtype code of a torch tensor: 1-D 4-byte -> u32, 1-D 8-byte -> u64,
+    2-D with 16-byte rows -> rec128."""
+    if A.dim() == 1 and A.element_size() in (4, 8):
+        return U32 if A.element_size() == 4 else U64
+    if A.dim() == 2 and A.element_size() * A.shape[1] == 16:
+        return REC128
+    raise ValueError("expected a 1-D tensor of 4- or 8-byte elements, or 2-D with 16-byte rows")
+
+
+def shuffle_ptr(ptr: int, n: int, dtype: int, seed: int, eps: float, *, H_ptr: int | None = None,
+                options: Options | None = None, aux_ptr: int | None = None, aux_bytes_: int = 0,
+                stats_ptr: int | None = None, stream: int = 0) -> None:
+    """Raw-pointer form of :func:`shuffle` (device pointers as integers)."""
+    rc = lib().pip_shuffle_ex(ptr, n, dtype, seed, H_ptr, eps, _opt_ptr(options), aux_ptr, aux_bytes_,
+                              stats_ptr, stream)
+    _raise(rc, "pip_shuffle_ex")
+
+
+def shuffle(A, seed: int = 0, eps: float = 0.5, *, H=None, stream=None, aux=None, stats=None, **options) -> None:
+    """Knuth-shuffle the CUDA tensor ``A`` in place (asynchronous on ``stream``).
+
+    ``H``: optional CUDA uint32/int32 tensor of explicit targets (0 <= H[i] <= i).
+    ``aux``: optional CUDA uint8 tensor used as scratch instead of allocating.
+    ``stats``: optional CUDA uint8 tensor of at least ``STATS_BYTES`` that the
+    kernel fills with a ``Stats`` record.  Other keywords are ``Options`` fields.
+    """
+    if not A.is_cuda or not A.is_contiguous():
+        raise ValueError("A must be a contiguous CUDA tensor")
+    d = tensor_dtype(A)
+    n = A.shape[0]
+    h_ptr = None
+    if H is not None:
+        if not H.is_cuda or H.element_size() != 4 or H.dim() != 1 or H.shape[0] != n or not H.is_contiguous():
+            raise ValueError("H must be a contiguous 1-D CUDA tensor of n 4-byte targets")
+        h_ptr = H.data_ptr()
+    aux_ptr, aux_n = (aux.data_ptr(), aux.numel() * aux.element_size()) if aux is not None else (None, 0)
+    st_ptr = None
+    if stats is not None:
+        if stats.numel() * stats.element_size() < STATS_BYTES:
+            raise ValueError("stats buffer too small")
+        st_ptr = stats.data_ptr()
+    shuffle_ptr(A.data_ptr(), n, d, seed, eps, H_ptr=h_ptr, options=make_options(**options), aux_ptr=aux_ptr,
+                aux_bytes_=aux_n, stats_ptr=st_ptr, stream=_stream_handle(stream))
+
+
+def check(stream=None) -> None:
+    """Synchronize ``stream`` and raise if device-side work reported an error."""
+    _raise(lib().pip_check(_stream_handle(stream)), "pip_check")
+
+
+def read_stats(buf) -> Stats:
+    """Decode a stats buffer filled by :func:`shuffle` (synchronizes via .cpu())."""
+    raw = bytes(buf.cpu().numpy().tobytes()[:STATS_BYTES])
+    return Stats.from_buffer_copy(raw)
+
+
+def version() -> str:
+    return lib().pip_version().decode()

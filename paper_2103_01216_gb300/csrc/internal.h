@@ -1,0 +1,88 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pip.h"
+
+namespace pip {
+
+// Byte layout of one shuffle's device scratch ("aux").  All offsets are
+// 256-byte aligned.  Ctrl words come first so a single memset clears them
+// together with the reservation tables.
+struct Ctrl {
+  uint32_t cnt[3];              // loser counters, rotating by round
+  uint32_t status;              // first device-side error of this call
+  unsigned long long barrier;   // monotone arrival counter of the grid barrier
+  uint32_t pad[58];
+};
+static_assert(sizeof(Ctrl) == 256, "ctrl block is one 256-byte line pair");
+
+struct Plan {
+  uint32_t n = 0;
+  uint32_t elem_bytes = 0;
+  double eps = 0.5;
+  uint32_t F = 0;          // fresh swaps per round
+  uint32_t kmax = 0;       // cap on active swaps per round
+  uint32_t nslots = 0;     // reservation slots per table
+  uint32_t blocks = 0;     // persistent grid blocks
+  uint32_t threads = 0;    // threads per block
+  uint64_t timeout_ns = 0;
+  uint64_t deadline_ns = 0;
+  uint32_t flags = 0;
+  // aux layout
+  uint64_t off_S[3] = {0, 0, 0};
+  uint64_t off_D[3] = {0, 0, 0};
+  uint64_t off_Q[2] = {0, 0};
+  uint64_t aux_bytes = 0;
+  uint64_t aux_bound = 0;
+};
+
+// Kernel arguments of the persistent round driver.
+struct GridArgs {
+  void* A;
+  const uint32_t* H;   // explicit targets, or nullptr for hashed targets
+  uint64_t seed;
+  uint32_t n;
+  uint32_t F;
+  uint32_t kmax;
+  uint32_t nslots;
+  uint32_t* S[3];
+  uint32_t* D[3];
+  uint32_t* Q[2];
+  Ctrl* ctrl;
+  pip_stats* stats;    // may be nullptr
+  uint64_t timeout_ns;
+  uint32_t max_rounds;
+  uint32_t flags;
+  uint32_t* latch;     // per-device error latch
+  uint64_t deadline_ns;  // whole-kernel time limit
+};
+
+// Device facts cached per device.
+struct DeviceInfo {
+  int sms = 0;
+  int max_threads_per_sm = 0;
+  size_t l2_bytes = 0;
+};
+pip_status device_info(DeviceInfo* out);
+
+// Planner (planner.cpp).
+pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options* opt, Plan* out);
+uint32_t elem_bytes_of(pip_dtype dtype);
+
+// Round driver launch (grid_driver.cu).  Queues the explicit-target
+// validation (if H is given), then the persistent kernel, on `stream`.
+pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint64_t seed,
+                              void* aux, pip_stats* stats, cudaStream_t stream);
+// Device address of the per-device error latch (current device), or nullptr.
+uint32_t* error_latch_ptr();
+// Reads and clears the latch of the current device (synchronous).
+pip_status take_error_latch(uint32_t* value);
+
+// Largest co-resident block count for the driver with this element size and
+// block size (cached per device).
+uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t threads);
+
+}  // namespace pip

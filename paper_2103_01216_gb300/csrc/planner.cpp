@@ -1,0 +1,169 @@
+// Host planner: turns (n, dtype, eps, overrides) into the prefix size, table
+// sizes, grid shape and the exact scratch layout of one shuffle.
+//
+// The relaxed PIP model (Section 3.2) allows O(n^(1-eps)) auxiliary space,
+// and Theorem 4.1 / 4.2 process a prefix of n^(1-eps) swaps per round.  The
+// library fixes the constant: every plan's scratch is at most
+// PIP_AUX_C * n^(1-eps) + 4096 bytes, and the prefix F is the largest
+// multiple of n^(1-eps) (capped by the option prefix_c, and by what keeps the
+// hot reservation tables inside L2) that fits.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <mutex>
+
+#include "internal.h"
+
+namespace pip {
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+constexpr double kDefaultPrefixC = 1.0;
+constexpr uint32_t kDefaultSlotFactor = 4;
+constexpr uint32_t kDefaultThreads = 512;
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
+constexpr uint32_t kItemsPerThread = 2;  // target positions per thread per round when sizing the grid
+
+uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+uint32_t kmax_of(uint32_t F) { return F + (F + 3) / 4; }  // room for ~25% carried losers
+
+// Fills the layout fields for a given F and slot factor; returns aux bytes.
+uint64_t layout(Plan* p, uint32_t F, uint32_t slot_factor) {
+  p->F = F;
+  p->kmax = kmax_of(F);
+  const uint64_t ns = (uint64_t)slot_factor * p->kmax;
+  p->nslots = (uint32_t)std::min<uint64_t>(ns, 0xFFFFFFF0ull);
+  uint64_t off = align_up(sizeof(Ctrl));
+  for (int j = 0; j < 3; ++j) {
+    p->off_S[j] = off;
+    off += align_up(4ull * p->nslots);
+  }
+  for (int j = 0; j < 3; ++j) {
+    p->off_D[j] = off;
+    off += align_up(4ull * p->F);
+  }
+  for (int j = 0; j < 2; ++j) {
+    p->off_Q[j] = off;
+    off += align_up(4ull * p->kmax);
+  }
+  p->aux_bytes = off;
+  return off;
+}
+
+std::mutex g_dev_mu;
+DeviceInfo g_dev[64];
+bool g_dev_ok[64] = {};
+
+}  // namespace
+
+pip_status device_info(DeviceInfo* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PIP_ECUDA;
+  }
+  if (dev < 0 || dev >= 64) return PIP_ECUDA;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_dev_ok[dev]) {
+    DeviceInfo d;
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&d.max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return PIP_ECUDA;
+    }
+    d.l2_bytes = (size_t)l2;
+    g_dev[dev] = d;
+    g_dev_ok[dev] = true;
+  }
+  *out = g_dev[dev];
+  return PIP_OK;
+}
+
+uint32_t elem_bytes_of(pip_dtype dtype) {
+  switch (dtype) {
+    case PIP_U32: return 4;
+    case PIP_U64: return 8;
+    case PIP_REC128: return 16;
+    default: return 0;
+  }
+}
+
+pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options* opt, Plan* out) {
+  const uint32_t eb = elem_bytes_of(dtype);
+  if (eb == 0 || !(eps > 0.0 && eps < 1.0) || n >= (1ull << 32) || n < 2) return PIP_EINVAL;
+  pip_options o{};
+  if (opt != nullptr) o = *opt;
+  Plan p;
+  p.n = (uint32_t)n;
+  p.elem_bytes = eb;
+  p.eps = eps;
+  p.flags = o.flags;
+
+  const double x = std::pow((double)n, 1.0 - eps);  // n^(1-eps)
+  p.aux_bound = (uint64_t)std::floor(PIP_AUX_C * x) + 4096;
+
+  uint32_t slot_factor = o.slot_factor ? o.slot_factor : kDefaultSlotFactor;
+  if (slot_factor < 2 || slot_factor > 16) return PIP_EINVAL;
+  uint32_t threads = o.block_threads ? o.block_threads : kDefaultThreads;
+  if (threads < 128 || threads > 1024 || threads % 32 != 0) return PIP_EINVAL;
+  p.threads = threads;
+
+  // requested prefix
+  double want;
+  if (o.fresh_per_round) {
+    want = (double)o.fresh_per_round;
+  } else {
+    const double c = o.prefix_c > 0.0 ? o.prefix_c : kDefaultPrefixC;
+    want = c * x;
+  }
+  uint64_t F = (uint64_t)std::max(1.0, std::ceil(want));
+  F = std::min<uint64_t>(F, n - 1);
+  // the hot tables (the one read and the one reserved into each round) stay
+  // within half of L2 unless the caller fixed F explicitly
+  DeviceInfo di;
+  const bool have_dev = device_info(&di) == PIP_OK;
+  if (!o.fresh_per_round && !(o.prefix_c > 0.0) && have_dev && di.l2_bytes > 0) {
+    const uint64_t hot_cap = di.l2_bytes / 2;
+    const uint64_t per_F = 2ull * 4ull * slot_factor * 5ull / 4ull;  // 2 tables * 4 B * slots per F
+    F = std::max<uint64_t>(1, std::min<uint64_t>(F, hot_cap / per_F));
+  }
+  // shrink until the scratch obeys the bound
+  while (layout(&p, (uint32_t)F, slot_factor) > p.aux_bound && F > 1) {
+    const double ratio = (double)p.aux_bound / (double)p.aux_bytes;
+    uint64_t nf = (uint64_t)std::floor((double)F * std::min(ratio, 0.999));
+    F = std::max<uint64_t>(1, std::min<uint64_t>(nf, F - 1));
+  }
+  if (p.aux_bytes > p.aux_bound) return PIP_EINVAL;  // cannot happen for n >= 2: F=1 needs ~2.3 KB
+
+  // grid: enough threads for ~kItemsPerThread active swaps each, at most what
+  // can be co-resident (a cooperative launch needs every block resident)
+  uint32_t maxb = have_dev ? grid_driver_max_blocks(eb, false, threads) : 0;
+  uint64_t want_blocks = (p.kmax + (uint64_t)threads * kItemsPerThread - 1) / ((uint64_t)threads * kItemsPerThread);
+  if (o.grid_blocks) want_blocks = o.grid_blocks;
+  want_blocks = std::max<uint64_t>(1, want_blocks);
+  if (maxb) want_blocks = std::min<uint64_t>(want_blocks, maxb);
+  p.blocks = (uint32_t)want_blocks;
+
+  uint64_t tmo = o.wait_timeout_ns ? o.wait_timeout_ns : kDefaultTimeoutNs;
+  if (const char* e = std::getenv("PIP_WAIT_TIMEOUT_MS")) {
+    const long long ms = std::atoll(e);
+    if (ms > 0 && !o.wait_timeout_ns) tmo = (uint64_t)ms * 1000000ull;
+  }
+  p.timeout_ns = tmo;
+  // whole-run limit: far above any legitimate run (about 1 us per round plus
+  // 1 ns per element would already be slow), so only a defect can reach it
+  uint64_t deadline = 60000000000ull + 2000ull * (p.n / p.F + 1) + 20ull * p.n;
+  if (const char* e = std::getenv("PIP_DEADLINE_MS")) {
+    const long long ms = std::atoll(e);
+    if (ms > 0) deadline = (uint64_t)ms * 1000000ull;
+  }
+  p.deadline_ns = deadline;
+  *out = p;
+  return PIP_OK;
+}
+
+}  // namespace pip

@@ -1,0 +1,100 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+function that include/pip.h declares, and its planner keeps the scratch bound
+of the relaxed PIP model (Section 3.2; Theorem 4.2)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "pip.h")
+
+
+@pytest.fixture(scope="module")
+def pip():
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    import paper_2103_01216_gb300 as pip
+
+    pip.lib()
+    return pip
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(pip_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pip_shuffle", "pip_shuffle_explicit_h", "pip_shuffle_ex", "pip_plan",
+                     "pip_aux_bytes", "pip_check", "pip_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(pip):
+    L = pip.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(pip):
+    L = pip.lib()
+    for code in range(8):
+        assert L.pip_status_string(code)
+    assert b"sm_103a" in L.pip_version()
+
+
+def test_argument_errors_are_reported_before_any_launch(pip):
+    L = pip.lib()
+    # eps outside (0,1), n >= 2^32, bad dtype, null A: all EINVAL without touching a GPU
+    assert L.pip_shuffle(ctypes.c_void_p(256), 10, 1, 0, 0.0, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle(ctypes.c_void_p(256), 10, 1, 0, 1.0, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle(ctypes.c_void_p(256), 1 << 32, 1, 0, 0.5, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle(ctypes.c_void_p(256), 10, 7, 0, 0.5, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle(None, 10, 1, 0, 0.5, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle(ctypes.c_void_p(260), 10, 1, 0, 0.5, None) == pip.PIP_EINVAL  # misaligned u64
+    assert L.pip_shuffle_explicit_h(ctypes.c_void_p(256), 10, 1, None, 0.5, None) == pip.PIP_EINVAL
+    # n <= 1 is a no-op
+    assert L.pip_shuffle(None, 0, 1, 0, 0.5, None) == pip.PIP_OK
+    assert L.pip_shuffle(ctypes.c_void_p(256), 1, 1, 0, 0.5, None) == pip.PIP_OK
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "rec128"])
+@pytest.mark.parametrize("eps", [0.1, 0.25, 0.5, 0.75, 0.9])
+@pytest.mark.parametrize("n", [2, 3, 100, 4097, 1 << 20, 10**9, 1 << 30, (1 << 32) - 1])
+def test_plan_obeys_the_aux_bound(pip, dtype, eps, n):
+    p = pip.plan(n, dtype, eps)
+    x = n ** (1.0 - eps)
+    assert p["aux_bound_bytes"] == math.floor(pip.AUX_C * x) + 4096
+    assert p["aux_bytes"] <= p["aux_bound_bytes"]
+    assert 1 <= p["fresh_per_round"] <= n - 1
+    assert p["max_active"] >= p["fresh_per_round"]
+    assert p["slots"] >= 2 * p["max_active"]
+    assert p["min_rounds"] == -(-(n - 1) // p["fresh_per_round"])
+    assert pip.aux_bytes(n, dtype, eps) == p["aux_bytes"]
+
+
+def test_plan_prefix_tracks_n_to_the_one_minus_eps(pip):
+    # with the default prefix constant the prefix is Theta(n^(1-eps)) (bound-limited)
+    for eps in (0.25, 0.5, 0.75):
+        for n in (1 << 16, 1 << 22, 1 << 28):
+            F = pip.plan(n, "u64", eps)["fresh_per_round"]
+            x = n ** (1.0 - eps)
+            assert 0.25 * x <= F <= 1.0 * x + 1
+
+
+def test_plan_overrides(pip):
+    p = pip.plan(1 << 20, "u64", 0.5, fresh_per_round=7, slot_factor=8, grid_blocks=3, block_threads=256)
+    assert p["fresh_per_round"] == 7 and p["slots"] == 8 * p["max_active"]
+    assert p["grid_blocks"] == 3 and p["block_threads"] == 256
+    with pytest.raises(pip.PipError):
+        pip.plan(1 << 20, "u64", 0.5, slot_factor=1)
+    with pytest.raises(pip.PipError):
+        pip.plan(1 << 20, "u64", 0.5, block_threads=100)

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA round driver against the CPU oracle, bit for bit.
+
+Every case runs the C ABI (through the Python binding) on a GB300 and compares
+the whole output array with the sequential Knuth shuffle of ``oracle/`` on the
+same input and the same targets.  The tolerance is zero: a shuffle has exactly
+one correct output for given targets.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.gpu_util import gpu_shuffle, load_pip, torch_cuda
+from tests.conftest import read_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pip():
+    torch_cuda()
+    return load_pip()
+
+
+def expect_hashed(arr, seed):
+    out = arr.copy()
+    oracle.knuth_hash(out, seed)
+    return out
+
+
+def expect_explicit(arr, H):
+    out = arr.copy()
+    oracle.knuth_explicit(out, H)
+    return out
+
+
+# ------------------------------------------------------------------ explicit targets
+@pytest.mark.parametrize("F", [1, 2, 3, 8])
+def test_figure3_worked_example(pip, F):
+    g = read_golden("fig3_worked_example.txt")
+    H = np.array([int(x) for x in g["h_zero_based"].split()], dtype=np.uint32)
+    expected = [int(x) for x in g["expected_output_zero_based"].split()]
+    for dt in ("u32", "u64"):
+        out, stats = gpu_shuffle(pip, workloads.iota(8, dt), H=H, fresh_per_round=F, with_stats=True)
+        assert out.tolist() == expected
+        assert stats.status == 0
+        assert stats.attempts == 7 + stats.losers
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_every_target_sequence_small_n(pip, n):
+    for F in sorted({1, 2, n - 1}):
+        for Ht in itertools.product(*[range(i + 1) for i in range(n)]):
+            H = np.array(Ht, dtype=np.uint32)
+            arr = workloads.iota(n, "u64")
+            out, _ = gpu_shuffle(pip, arr, H=H, fresh_per_round=F)
+            assert np.array_equal(out, expect_explicit(arr, H)), (F, Ht)
+
+
+@pytest.mark.slow
+def test_every_target_sequence_n7(pip):
+    n = 7
+    seen = set()
+    for Ht in itertools.product(*[range(i + 1) for i in range(n)]):
+        H = np.array(Ht, dtype=np.uint32)
+        arr = workloads.iota(n, "u32")
+        out, _ = gpu_shuffle(pip, arr, H=H, fresh_per_round=3)
+        assert np.array_equal(out, expect_explicit(arr, H)), Ht
+        seen.add(tuple(out.tolist()))
+    assert len(seen) == 5040  # the bijection, seen through the GPU path
+
+
+def closed_form_targets(n):
+    return {
+        "zero": np.zeros(n, dtype=np.uint32),
+        "prev": np.maximum(np.arange(n, dtype=np.int64) - 1, 0).astype(np.uint32),
+        "self": np.arange(n, dtype=np.uint32),
+    }
+
+
+@pytest.mark.parametrize("n", [2, 3, 1000, 20011])
+@pytest.mark.parametrize("F", [1, 7, 4096])
+def test_closed_form_worst_cases(pip, n, F):
+    for name, H in closed_form_targets(n).items():
+        arr = workloads.iota(n, "u64")
+        out, stats = gpu_shuffle(pip, arr, H=H, fresh_per_round=F, with_stats=True)
+        if name == "zero":
+            assert out.tolist() == [(i + 1) % n for i in range(n)]
+            assert stats.rounds == n - 1  # depth n-1 chain: exactly one commit per round
+        elif name == "prev":
+            assert out.tolist() == [n - 1] + list(range(n - 1))
+            assert stats.rounds == n - 1
+        else:
+            assert out.tolist() == list(range(n))
+        assert stats.attempts == (n - 1) + stats.losers
+
+
+@pytest.mark.parametrize("n", [5, 1001, 65539])
+def test_sattolo_targets(pip, n):
+    rng = np.random.default_rng(n)
+    H = np.zeros(n, dtype=np.uint32)
+    H[1:] = np.floor(rng.random(n - 1) * np.arange(1, n)).astype(np.uint32)  # strictly below i
+    arr = workloads.iota(n, "u32")
+    out, _ = gpu_shuffle(pip, arr, H=H, fresh_per_round=max(1, n // 50))
+    assert np.array_equal(out, expect_explicit(arr, H))
+
+
+@pytest.mark.parametrize("n,F", [(1000, 1), (1000, 64), (65537, 256), (300007, 4096), (1 << 20, 100000)])
+def test_random_explicit_targets(pip, n, F):
+    H = workloads.random_targets(n, rng_seed=n + F)
+    arr = workloads.iota(n, "u64")
+    out, stats = gpu_shuffle(pip, arr, H=H, fresh_per_round=F, with_stats=True)
+    assert np.array_equal(out, expect_explicit(arr, H))
+    assert stats.rounds >= -(-(n - 1) // F)
+    assert stats.attempts == (n - 1) + stats.losers
+
+
+# ------------------------------------------------------------------ hashed targets
+def test_config_2pow20_u64_seed1_eps_half(pip):
+    n = 1 << 20
+    arr = workloads.iota(n, "u64")
+    out, stats = gpu_shuffle(pip, arr, seed=1, eps=0.5, with_stats=True)
+    assert np.array_equal(out, expect_hashed(arr, 1))
+    assert stats.status == 0 and stats.attempts == (n - 1) + stats.losers
+    p = pip.plan(n, "u64", 0.5)
+    assert stats.rounds >= p["min_rounds"]
+    assert stats.max_active <= p["max_active"]
+
+
+@pytest.mark.parametrize("n", [2, 3, 31, 32, 33, 1023, 1025, 4097, 100003])
+@pytest.mark.parametrize("dtype", ["u32", "u64", "rec128"])
+def test_ragged_sizes_all_dtypes(pip, n, dtype):
+    arr = workloads.make(n, dtype)
+    seed = 1000 + n
+    out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5)
+    assert np.array_equal(out, expect_hashed(arr, seed))
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.25, 0.5, 0.75, 0.9])
+def test_eps_sweep(pip, eps):
+    n = (1 << 18) + 13
+    arr = workloads.iota(n, "u64")
+    out, stats = gpu_shuffle(pip, arr, seed=7, eps=eps, with_stats=True)
+    assert np.array_equal(out, expect_hashed(arr, 7))
+    p = pip.plan(n, "u64", eps)
+    assert p["aux_bytes"] <= p["aux_bound_bytes"]
+    assert stats.max_active <= p["max_active"]
+
+
+def test_output_does_not_depend_on_launch_shape(pip):
+    n, seed = 300007, 11
+    arr = workloads.iota(n, "u32")
+    ref = expect_hashed(arr, seed)
+    configs = [
+        dict(fresh_per_round=13),
+        dict(fresh_per_round=1000, slot_factor=2),
+        dict(fresh_per_round=1000, slot_factor=16),
+        dict(fresh_per_round=50000, grid_blocks=1),
+        dict(fresh_per_round=50000, grid_blocks=2, block_threads=128),
+        dict(fresh_per_round=50000, block_threads=1024),
+        dict(fresh_per_round=n - 1),
+        dict(prefix_c=0.01),
+    ]
+    for c in configs:
+        out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5, **c)
+        assert np.array_equal(out, ref), c
+
+
+def test_records_keep_their_payload(pip):
+    n, seed = (1 << 19) + 7, 3
+    arr = workloads.records(n)
+    out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5)
+    assert np.array_equal(out, expect_hashed(arr, seed))
+    assert np.array_equal(out[:, 1], workloads.record_payload(out[:, 0]))
+
+
+def test_deterministic_repeat(pip):
+    n = 200003
+    arr = workloads.iota(n, "u64")
+    a, _ = gpu_shuffle(pip, arr, seed=5, eps=0.4)
+    b, _ = gpu_shuffle(pip, arr, seed=5, eps=0.4)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("eps", [0.25, 0.5, 0.75])
+def test_2pow24_against_oracle(pip, eps):
+    n = 1 << 24
+    arr = workloads.iota(n, "u64")
+    out, stats = gpu_shuffle(pip, arr, seed=2, eps=eps, with_stats=True)
+    assert np.array_equal(out, expect_hashed(arr, 2))
+    assert stats.attempts == (n - 1) + stats.losers
+
+
+# ------------------------------------------------------------------ errors
+def test_invalid_explicit_targets_leave_array_untouched(pip):
+    torch = torch_cuda()
+    from tests.gpu_util import to_dev, from_dev
+
+    n = 4096
+    arr = workloads.iota(n, "u64")
+    H = workloads.random_targets(n, 3)
+    H[1234] = 1300  # > i
+    A = to_dev(arr)
+    pip.shuffle(A, H=to_dev(H), eps=0.5)
+    with pytest.raises(pip.PipError) as e:
+        pip.check()
+    assert e.value.code == pip.PIP_EINVAL
+    assert np.array_equal(from_dev(A, arr), arr)
+    # the latch was cleared and the library keeps working
+    out, _ = gpu_shuffle(pip, arr, seed=1, eps=0.5)
+    assert np.array_equal(out, expect_hashed(arr, 1))
+    del torch
+
+
+def test_barrier_wait_runs_out_and_reports_timeout(pip):
+    """A block that never arrives makes every bounded wait give up (no hang)."""
+    from tests.gpu_util import to_dev, from_dev
+
+    n = 1 << 16
+    arr = workloads.iota(n, "u64")
+    A = to_dev(arr)
+    pip.shuffle(A, seed=1, eps=0.5, grid_blocks=4, flags=pip.FLAG_TEST_SKIP_BARRIER,
+                wait_timeout_ns=50_000_000)
+    with pytest.raises(pip.PipError) as e:
+        pip.check()
+    assert e.value.code == pip.PIP_ETIMEOUT
+    assert np.array_equal(from_dev(A, arr), arr)
+    out, _ = gpu_shuffle(pip, arr, seed=1, eps=0.5)
+    assert np.array_equal(out, expect_hashed(arr, 1))
+
+
+def test_caller_provided_scratch(pip):
+    torch = torch_cuda()
+    from tests.gpu_util import to_dev, from_dev
+
+    n = 1 << 18
+    arr = workloads.iota(n, "u32")
+    p = pip.plan(n, "u32", 0.5)
+    aux = torch.empty(p["aux_bytes"], dtype=torch.uint8, device="cuda")
+    A = to_dev(arr)
+    pip.shuffle(A, seed=9, eps=0.5, aux=aux)
+    pip.check()
+    assert np.array_equal(from_dev(A, arr), expect_hashed(arr, 9))
+    small = torch.empty(p["aux_bytes"] - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pip.PipError):
+        pip.shuffle(A, seed=9, eps=0.5, aux=small)

@@ -44,10 +44,11 @@ def test_swap_target_range_and_composition():
     # composition H[i] = floor(splitmix64(seed ^ i) * (i + 1) / 2^64), spot-checked
     # on the published vector's state so both factors are pinned externally
     state = int(g["seed"])
-    first = int(g["outputs"].split()[0])
-    for i in (0, 1, 7, 1000):
-        seed = state ^ i
-        assert oracle.swap_target(seed, i) == (first * (i + 1)) >> 64
+    for out in map(int, g["outputs"].split()):
+        for i in range(0, 300):
+            # seed chosen so that seed ^ i is the published state
+            assert oracle.swap_target(state ^ i, i) == (out * (i + 1)) >> 64
+        state = (state + 0x9E3779B97F4A7C15) & M64
     for seed in (0, 1, 2, 3, 0xDEADBEEF):
         H = oracle.swap_targets(seed, 5000)
         assert H[0] == 0

@@ -66,10 +66,16 @@ def _pins_pass(L):
     for a, b in [(2**64 - 1, 2**64 - 1), (12345678901234567, 98765432109876543)]:
         if L.oracle_mulhi64(a, b) != (a * b) >> 64:
             return False
-    first = int(g["outputs"].split()[0])
-    for i in (1, 7, 1000):
-        if L.oracle_swap_target(int(g["seed"]) ^ i, i) != (first * (i + 1)) >> 64:
-            return False
+    # H[i] = floor(splitmix64(seed ^ i) * (i + 1) / 2^64) on the published states
+    s = int(g["seed"])
+    for o in map(int, g["outputs"].split()):
+        for i in range(1, 200):
+            if L.oracle_swap_target(s ^ i, i) != (o * (i + 1)) >> 64:
+                return False
+        s = (s + 0x9E3779B97F4A7C15) & ((1 << 64) - 1)
+    # the top of the range, H[i] = i, is reachable
+    if sum(L.oracle_swap_target(5, i) == i for i in range(1, 40000)) < 3:
+        return False
     f3 = read_golden("fig3_worked_example.txt")
     h0 = np.array([int(x) for x in f3["h_zero_based"].split()], dtype=np.uint32)
     A = np.arange(8, dtype=np.uint64)
