@@ -260,6 +260,7 @@ def main():
     ap.add_argument("--slot-factor", type=int, default=0)
     ap.add_argument("--grid-blocks", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--flags", type=int, default=0, help="PIP_FLAG_* bits (2 = L2 prefetch of the next block)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -297,6 +298,8 @@ def main():
         opts["grid_blocks"] = args.grid_blocks
     if args.block_threads:
         opts["block_threads"] = args.block_threads
+    if args.flags:
+        opts["flags"] = args.flags
 
     n, dtype, seed, eps = args.n, args.dtype, args.seed, args.eps
     plan = pip.plan(n, dtype, eps, **opts)

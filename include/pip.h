@@ -72,6 +72,9 @@ typedef struct {
     uint64_t aux_bytes;        /* exact device scratch bytes this plan allocates */
     uint64_t aux_bound_bytes;  /* c*n^(1-eps) + 4096 with c = PIP_AUX_C: the bound aux_bytes obeys */
     uint64_t min_rounds;       /* ceil((n-1)/F): a lower bound on the rounds */
+    uint32_t driver;           /* 0 = persistent grid, 1 = one block with shared-memory tables */
+    uint32_t pad;
+    uint64_t smem_bytes;       /* on-chip scratch of the one-block driver (counted in the bound) */
 } pip_plan_info;
 
 /* Aux constant c (bytes per unit of n^(1-eps)) that every plan obeys. */
@@ -83,7 +86,7 @@ typedef struct {
     uint32_t fresh_per_round;  /* explicit F (overrides prefix_c; still clamped by the bound) */
     uint32_t slot_factor;      /* reservation slots per active swap (2..16, default 4) */
     uint32_t grid_blocks;      /* persistent blocks (clamped to what can be co-resident) */
-    uint32_t block_threads;    /* 128..1024, multiple of 32 */
+    uint32_t block_threads;    /* 128..512, multiple of 32 */
     uint64_t wait_timeout_ns;  /* limit of each device-side barrier wait (default 2e9 ns) */
     uint32_t flags;            /* PIP_FLAG_* */
 } pip_options;
@@ -92,6 +95,19 @@ typedef struct {
  * bounded wait runs out and the call reports PIP_ETIMEOUT.  The array is left
  * untouched (the hook fires before any swap). */
 #define PIP_FLAG_TEST_SKIP_BARRIER 1u
+/* Prefetch into L2, one round ahead, the array lines the next fresh block
+ * will swap. */
+#define PIP_FLAG_PREFETCH 2u
+/* L2 eviction priorities: the array's lines evict-first, the reservation
+ * tables' lines evict-last.  Performance hints only; results are identical. */
+#define PIP_FLAG_ARRAY_EVICT_FIRST 4u
+#define PIP_FLAG_TABLE_EVICT_LAST 8u
+/* Only the array stores are marked evict-first (loads keep the normal policy). */
+#define PIP_FLAG_ARRAY_STORE_EVICT_FIRST 16u
+/* Driver selection: by default arrays whose prefix fits in one block's shared
+ * memory run on one block, larger prefixes on the persistent grid. */
+#define PIP_FLAG_FORCE_GRID 32u
+#define PIP_FLAG_FORCE_CTA 64u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {
@@ -103,6 +119,40 @@ typedef struct {
     uint32_t grid_blocks;     /* blocks that ran */
     uint64_t reserved[4];
 } pip_stats;
+
+/* Per-array statistics of a batched run. */
+typedef struct {
+    uint32_t status;
+    uint32_t rounds;
+    uint64_t attempts;
+    uint64_t losers;
+    uint32_t max_active;
+    uint32_t pad;
+} pip_job_stats;
+
+/* One array of a batch. */
+typedef struct {
+    void *A_dev;              /* device array of n elements (caller-owned) */
+    const uint32_t *H_dev;    /* explicit targets, or NULL for hashed targets */
+    uint64_t n;               /* < 2^32 */
+    uint64_t seed;            /* hashed-target seed */
+} pip_batch_item;
+
+/* Launch plan of a batch (host struct, filled by pip_batch_plan_make). */
+typedef struct {
+    uint32_t count;
+    uint32_t elem_bytes;
+    uint32_t fmax;            /* largest per-array fresh block */
+    uint32_t slot_factor;
+    uint32_t block_threads;
+    uint32_t max_blocks;      /* 0 = as many as fit */
+    uint32_t any_explicit;
+    uint32_t pad;
+    uint64_t jobs_bytes;      /* device bytes of the job list (pip_batch_prepare) */
+    uint64_t smem_bytes;      /* shared memory per block */
+    uint64_t total_elems;
+    double eps;
+} pip_batch_plan;
 
 /*
  * pip_shuffle -- in-place Knuth shuffle of A_dev[0..n) with hashed targets
@@ -141,6 +191,40 @@ pip_status pip_shuffle_ex(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t see
                           const uint32_t *H_dev, double eps, const pip_options *opt,
                           void *aux_dev, uint64_t aux_bytes, pip_stats *stats_dev,
                           void *stream);
+
+/*
+ * pip_shuffle_batch -- shuffles `count` independent arrays in one persistent
+ * launch (spec batching pattern; each array is the method of Section
+ * 4.1 with its own targets H_j[i] = mulhi64(splitmix64(seeds[j] ^ i), i+1)).
+ *   A_devs, ns, seeds: host arrays of length count; A_devs[j] is a device
+ *                      array of ns[j] elements of `dtype`.
+ * Every array gets the same result as pip_shuffle(A_devs[j], ns[j], dtype,
+ * seeds[j], eps).  Builds the job list on the host (synchronous copy), then
+ * queues the launch on `stream`; the job list is freed stream-ordered.
+ */
+pip_status pip_shuffle_batch(void *const *A_devs, const uint64_t *ns, const uint64_t *seeds,
+                             uint32_t count, pip_dtype dtype, double eps, void *stream);
+
+/*
+ * Graph-capturable batch in three calls:
+ *   pip_batch_plan_make -- host-only planning of `items` (host array).
+ *   pip_batch_prepare   -- writes the job list (largest array first) into
+ *                          jobs_dev (plan->jobs_bytes device bytes, 256-byte
+ *                          aligned); synchronous.
+ *   pip_batch_run       -- queues the run on `stream`: a memset of the job
+ *                          list's counters and one kernel launch (plus a
+ *                          validation kernel when explicit targets are
+ *                          present).  May be captured into a CUDA graph and
+ *                          replayed; each replay shuffles every array again.
+ *   stats_dev: NULL or a device array of plan->count pip_job_stats, indexed
+ *              like `items`.
+ */
+pip_status pip_batch_plan_make(const pip_batch_item *items, uint32_t count, pip_dtype dtype, double eps,
+                               const pip_options *opt, pip_batch_plan *out);
+pip_status pip_batch_prepare(const pip_batch_item *items, const pip_batch_plan *plan,
+                             const pip_options *opt, void *jobs_dev);
+pip_status pip_batch_run(const pip_batch_plan *plan, void *jobs_dev, pip_job_stats *stats_dev,
+                         void *stream);
 
 /*
  * pip_plan -- the plan pip_shuffle_ex would use for these arguments on the

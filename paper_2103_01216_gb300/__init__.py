@@ -37,6 +37,7 @@ STATUS = {
 }
 PIP_OK, PIP_EINVAL, PIP_ENOMEM, PIP_ECUDA, PIP_ETIMEOUT, PIP_EAGAIN, PIP_EBUSY, PIP_EINTERNAL = range(8)
 FLAG_TEST_SKIP_BARRIER = 1
+FLAG_PREFETCH = 2
 AUX_C = 128.0
 
 
@@ -59,6 +60,46 @@ class PlanInfo(ctypes.Structure):
         ("aux_bytes", ctypes.c_uint64),
         ("aux_bound_bytes", ctypes.c_uint64),
         ("min_rounds", ctypes.c_uint64),
+        ("driver", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+        ("smem_bytes", ctypes.c_uint64),
+    ]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("A_dev", ctypes.c_void_p),
+        ("H_dev", ctypes.c_void_p),
+        ("n", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class BatchPlan(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_uint32),
+        ("elem_bytes", ctypes.c_uint32),
+        ("fmax", ctypes.c_uint32),
+        ("slot_factor", ctypes.c_uint32),
+        ("block_threads", ctypes.c_uint32),
+        ("max_blocks", ctypes.c_uint32),
+        ("any_explicit", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+        ("jobs_bytes", ctypes.c_uint64),
+        ("smem_bytes", ctypes.c_uint64),
+        ("total_elems", ctypes.c_uint64),
+        ("eps", ctypes.c_double),
+    ]
+
+
+class JobStats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_uint32),
+        ("rounds", ctypes.c_uint32),
+        ("attempts", ctypes.c_uint64),
+        ("losers", ctypes.c_uint64),
+        ("max_active", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
     ]
 
 
@@ -87,6 +128,13 @@ class Stats(ctypes.Structure):
 
 
 STATS_BYTES = ctypes.sizeof(Stats)
+JOB_STATS_BYTES = ctypes.sizeof(JobStats)
+DRIVER_GRID, DRIVER_CTA = 0, 1
+FLAG_ARRAY_EVICT_FIRST = 4
+FLAG_TABLE_EVICT_LAST = 8
+FLAG_ARRAY_STORE_EVICT_FIRST = 16
+FLAG_FORCE_GRID = 32
+FLAG_FORCE_CTA = 64
 
 _lock = threading.Lock()
 _lib = None
@@ -121,6 +169,17 @@ def lib() -> ctypes.CDLL:
         L.pip_status_string.restype = ctypes.c_char_p
         L.pip_version.argtypes = []
         L.pip_version.restype = ctypes.c_char_p
+        L.pip_shuffle_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(u64), u32, i32, dbl,
+                                        vp]
+        L.pip_shuffle_batch.restype = i32
+        L.pip_batch_plan_make.argtypes = [ctypes.POINTER(BatchItem), u32, i32, dbl, ctypes.POINTER(Options),
+                                          ctypes.POINTER(BatchPlan)]
+        L.pip_batch_plan_make.restype = i32
+        L.pip_batch_prepare.argtypes = [ctypes.POINTER(BatchItem), ctypes.POINTER(BatchPlan),
+                                        ctypes.POINTER(Options), vp]
+        L.pip_batch_prepare.restype = i32
+        L.pip_batch_run.argtypes = [ctypes.POINTER(BatchPlan), vp, vp, vp]
+        L.pip_batch_run.restype = i32
         _lib = L
         return L
 
@@ -228,3 +287,76 @@ def read_stats(buf) -> Stats:
 
 def version() -> str:
     return lib().pip_version().decode()
+
+
+# ---------------------------------------------------------------- batches
+def _items(arrays, seeds, H=None):
+    n = len(arrays)
+    items = (BatchItem * n)()
+    d = None
+    for j, A in enumerate(arrays):
+        if not A.is_cuda or not A.is_contiguous():
+            raise ValueError("every array must be a contiguous CUDA tensor")
+        dj = tensor_dtype(A)
+        if d is None:
+            d = dj
+        elif d != dj:
+            raise ValueError("all arrays of a batch share one element type")
+        items[j].A_dev = A.data_ptr()
+        items[j].n = A.shape[0]
+        items[j].seed = int(seeds[j])
+        if H is not None and H[j] is not None:
+            if H[j].element_size() != 4 or H[j].shape[0] != A.shape[0]:
+                raise ValueError("explicit targets must be n 4-byte entries")
+            items[j].H_dev = H[j].data_ptr()
+    return items, (d if d is not None else U64)
+
+
+class Batch:
+    """A prepared batch: plan + device job list, re-runnable and graph-capturable.
+
+    ``run()`` queues one shuffle of every array (a memset and one kernel).
+    """
+
+    def __init__(self, arrays, seeds, eps: float = 0.5, H=None, **options):
+        import torch
+
+        self.arrays = list(arrays)
+        self.items, self.dtype = _items(self.arrays, seeds, H)
+        self.options = make_options(**options)
+        self.plan = BatchPlan()
+        _raise(lib().pip_batch_plan_make(self.items, len(self.arrays), self.dtype, eps, _opt_ptr(self.options),
+                                         ctypes.byref(self.plan)), "pip_batch_plan_make")
+        self.jobs = torch.empty(max(256, self.plan.jobs_bytes), dtype=torch.uint8, device="cuda")
+        _raise(lib().pip_batch_prepare(self.items, ctypes.byref(self.plan), _opt_ptr(self.options),
+                                       self.jobs.data_ptr()), "pip_batch_prepare")
+
+    def run(self, stream=None, stats=None) -> None:
+        st = None
+        if stats is not None:
+            if stats.numel() * stats.element_size() < JOB_STATS_BYTES * len(self.arrays):
+                raise ValueError("stats buffer too small")
+            st = stats.data_ptr()
+        _raise(lib().pip_batch_run(ctypes.byref(self.plan), self.jobs.data_ptr(), st, _stream_handle(stream)),
+               "pip_batch_run")
+
+    def plan_dict(self) -> dict:
+        return {f: getattr(self.plan, f) for f, _ in BatchPlan._fields_}
+
+
+def shuffle_batch(arrays, seeds, eps: float = 0.5, stream=None) -> None:
+    """Shuffle every CUDA tensor of ``arrays`` in place in one launch
+    (``pip_shuffle_batch``); ``seeds[j]`` is array j's target seed."""
+    n = len(arrays)
+    if n == 0:
+        return
+    items, d = _items(arrays, seeds)
+    ptrs = (ctypes.c_void_p * n)(*[items[j].A_dev for j in range(n)])
+    ns = (ctypes.c_uint64 * n)(*[items[j].n for j in range(n)])
+    sd = (ctypes.c_uint64 * n)(*[items[j].seed for j in range(n)])
+    _raise(lib().pip_shuffle_batch(ptrs, ns, sd, n, d, eps, _stream_handle(stream)), "pip_shuffle_batch")
+
+
+def read_job_stats(buf, count: int):
+    raw = bytes(buf.cpu().numpy().tobytes()[: JOB_STATS_BYTES * count])
+    return [JobStats.from_buffer_copy(raw, j * JOB_STATS_BYTES) for j in range(count)]

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpip_gb300.so")
 
-SOURCES = ["grid_driver.cu", "pip_api.cu", "planner.cpp"]
+SOURCES = ["grid_driver.cu", "cta_driver.cu", "pip_api.cu", "planner.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -63,6 +63,7 @@ def build(force: bool = False, extra_flags: list[str] | None = None) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = list(extra_flags or [])
+    extra += os.environ.get("PIP_NVCC_FLAGS", "").split()
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"

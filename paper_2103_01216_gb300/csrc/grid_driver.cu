@@ -39,6 +39,10 @@
 // Self-loops (h == i) never reserve and finish at once (text under Alg. 1).
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "device.cuh"
 #include "internal.h"
@@ -52,15 +56,21 @@ __device__ uint32_t g_error_latch;
 namespace {
 
 constexpr uint32_t kLoserBuf = 2048;  // per-block staging of losers (8 KB)
+// Positions per thread in flight in the commit phase, and the launch bounds:
+// 32 registers and 2048 resident threads per SM measured best on GB300 (more
+// warps beat deeper per-thread batches for this random-access mix).
+#ifndef PIP_KU
+#define PIP_KU 2
+#endif
+#ifndef PIP_MIN_BLOCKS
+#define PIP_MIN_BLOCKS 4
+#endif
+#ifndef PIP_MAX_THREADS
+#define PIP_MAX_THREADS 512
+#endif
+constexpr int kU = PIP_KU;            // positions per thread in flight in the commit phase
 constexpr unsigned kFull = 0xffffffffu;
 
-template <typename Elem>
-__device__ __forceinline__ void swap_elems(Elem* A, uint32_t i, uint32_t h) {
-  const Elem x = ldcg(A + i);
-  const Elem y = ldcg(A + h);
-  stcg(A + i, y);
-  stcg(A + h, x);
-}
 
 template <bool kExplicit>
 __device__ __forceinline__ uint32_t target_of(const GridArgs& a, uint32_t i) {
@@ -71,30 +81,61 @@ __device__ __forceinline__ uint32_t target_of(const GridArgs& a, uint32_t i) {
 // Reserve target h for step i in the tables of a round whose fresh window is
 // [wlo, whi).
 __device__ __forceinline__ void reserve(uint32_t* D, uint32_t* S, uint32_t nslots, uint32_t wlo,
-                                        uint32_t whi, uint32_t h, uint32_t prio) {
-  if (h >= wlo && h < whi) atomicMax(D + (h - wlo), prio);
-  else atomicMax(S + slot_of(h, nslots), prio);
+                                        uint32_t whi, uint32_t h, uint32_t prio, uint64_t tpol) {
+  if (h >= wlo && h < whi) red_max_hint(D + (h - wlo), prio, tpol);
+  else red_max_hint(S + slot_of(h, nslots), prio, tpol);
 }
 
-template <bool kExplicit>
+// L2 policies of one thread: for the array and for the reservation tables.
+struct Policies {
+  uint64_t arr, arr_st, tab;
+};
+__device__ __forceinline__ Policies make_policies(uint32_t flags) {
+  Policies p;
+  p.arr = (flags & PIP_FLAG_ARRAY_EVICT_FIRST) ? policy_evict_first() : policy_evict_normal();
+  p.arr_st = (flags & (PIP_FLAG_ARRAY_EVICT_FIRST | PIP_FLAG_ARRAY_STORE_EVICT_FIRST)) ? policy_evict_first()
+                                                                                        : policy_evict_normal();
+  p.tab = (flags & PIP_FLAG_TABLE_EVICT_LAST) ? policy_evict_last() : policy_evict_normal();
+  return p;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Fresh block [lo, hi) reserves for the round whose window it is.  With
+// PIP_FLAG_PREFETCH the A lines that round will swap are pulled into L2 now,
+// one round ahead of the commit that reads them.
+template <typename Elem, bool kExplicit>
 __device__ __forceinline__ void reserve_fresh(const GridArgs& a, uint32_t lo, uint32_t hi,
-                                              uint32_t* D, uint32_t* S, uint32_t tid, uint32_t T) {
+                                              uint32_t* D, uint32_t* S, uint32_t tid, uint32_t T,
+                                              uint64_t tpol) {
+  const bool pf = (a.flags & PIP_FLAG_PREFETCH) != 0u;
+  const Elem* A = static_cast<const Elem*>(a.A);
+#pragma unroll 4
   for (uint32_t i = lo + tid; i < hi; i += T) {
     const uint32_t h = target_of<kExplicit>(a, i);
-    if (h != i) reserve(D, S, a.nslots, lo, hi, h, i + 1);
+    if (h != i) {
+      reserve(D, S, a.nslots, lo, hi, h, i + 1, tpol);
+      if (pf) {
+        prefetch_l2(A + h);
+        if ((i & 7u) == 0u || i == lo + tid) prefetch_l2(A + i);
+      }
+    }
   }
 }
 
-__device__ __forceinline__ void clear_words(uint32_t* p, uint32_t count, uint32_t tid, uint32_t T) {
+__device__ __forceinline__ void clear_words(uint32_t* p, uint32_t count, uint32_t tid, uint32_t T,
+                                            uint64_t tpol) {
   // 16-byte stores over the 16-byte aligned body, scalars for the tail
   const uint32_t n4 = count >> 2;
   uint4* p4 = reinterpret_cast<uint4*>(p);
-  for (uint32_t j = tid; j < n4; j += T) stcg(p4 + j, make_uint4(0, 0, 0, 0));
-  for (uint32_t j = (n4 << 2) + tid; j < count; j += T) stcg(p + j, 0u);
+  for (uint32_t j = tid; j < n4; j += T) st_hint(p4 + j, make_uint4(0, 0, 0, 0), tpol);
+  for (uint32_t j = (n4 << 2) + tid; j < count; j += T) st_hint(p + j, 0u, tpol);
 }
 
 template <typename Elem, bool kExplicit>
-__global__ void __launch_bounds__(1024) rounds_kernel(const GridArgs a) {
+__global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel(const GridArgs a) {
   __shared__ uint32_t s_lbuf[kLoserBuf];
   __shared__ uint32_t s_lcount, s_flush, s_base;
 
@@ -105,6 +146,7 @@ __global__ void __launch_bounds__(1024) rounds_kernel(const GridArgs a) {
   const uint32_t lane = threadIdx.x & 31u;
   uint64_t epoch = 0;
   const uint64_t t_start = globaltimer_ns();
+  const Policies pol = make_policies(a.flags);
 
   if (threadIdx.x == 0) s_lcount = 0;
   // an invalid explicit target sequence was reported by the validation pass
@@ -119,7 +161,7 @@ __global__ void __launch_bounds__(1024) rounds_kernel(const GridArgs a) {
     uint32_t m = f;
     uint64_t attempts = 0, losers_total = 0;
     uint32_t max_active = 0, rounds = 0;
-    reserve_fresh<kExplicit>(a, L, Lprev, a.D[0], a.S[0], tid, T);
+    reserve_fresh<Elem, kExplicit>(a, L, Lprev, a.D[0], a.S[0], tid, T, pol.tab);
     const bool arrive = !((a.flags & PIP_FLAG_TEST_SKIP_BARRIER) && blockIdx.x == 0);
     if (!grid_barrier(&ctrl->barrier, gridDim.x, epoch, &ctrl->status, a.timeout_ns, arrive)) goto done;
 
@@ -134,7 +176,9 @@ __global__ void __launch_bounds__(1024) rounds_kernel(const GridArgs a) {
       uint32_t* const cnt_out = &ctrl->cnt[b1];
 
       // next round's fresh block W_{r+1} = [Ln, L); throttled so that
-      // m_{r+1} <= (m_r - 1) + fn <= kmax (at least one swap of round r commits)
+      // m_{r+1} <= (m_r - 1) + fn <= kmax (at least one swap of round r
+      // commits), which bounds the loser queue; with kmax = 2.5 F the
+      // throttle only acts when more than half a block of losers piles up
       uint32_t fn = min(a.F, L - 1u);
       fn = min(fn, a.kmax - m + 1u);
       const uint32_t Ln = L - fn;
@@ -144,38 +188,75 @@ __global__ void __launch_bounds__(1024) rounds_kernel(const GridArgs a) {
         if (globaltimer_ns() - t_start > a.deadline_ns) set_status(&ctrl->status, PIP_ETIMEOUT);
       }
 
-      // ---- (a) commit round r
-      for (uint32_t p0 = tid & ~31u; p0 < m; p0 += T) {
-        const uint32_t p = p0 + lane;
-        bool lose = false;
-        uint32_t i = 0, h = 0;
-        if (p < m) {
-          i = (p < nl) ? ldcg(Qin + p) : L + (p - nl);
-          h = target_of<kExplicit>(a, i);
-          if (h != i) {
-            const bool own_free = (i < Lprev) ? (ldcg(Dr + (i - L)) == 0u)
-                                              : (ldcg(Sr + slot_of(i, a.nslots)) <= i + 1u);
-            const uint32_t rh = (h >= L && h < Lprev) ? ldcg(Dr + (h - L))
-                                                      : ldcg(Sr + slot_of(h, a.nslots));
-            if (own_free && rh == i + 1u) swap_elems(A, i, h);
-            else lose = true;
+      // ---- (a) commit round r.  Each thread takes kU positions at a time
+      // (p, p+T, ..., p+(kU-1)T) and issues their loads together so that kU
+      // independent memory chains are in flight per thread.
+      for (uint32_t p0 = tid & ~31u; p0 < m; p0 += kU * T) {
+        uint32_t ii[kU], hh[kU], own[kU], rh[kU];
+        bool act[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+          const uint32_t p = p0 + lane + (uint32_t)j * T;
+          act[j] = p < m;
+          ii[j] = 0;
+          if (act[j]) ii[j] = (p < nl) ? ld_hint(Qin + p, pol.tab) : L + (p - nl);
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+          hh[j] = act[j] ? target_of<kExplicit>(a, ii[j]) : 0u;
+          act[j] = act[j] && hh[j] != ii[j];  // self-loops finish at once
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+          own[j] = 0;
+          rh[j] = 0;
+          if (act[j]) {
+            const uint32_t i = ii[j], h = hh[j];
+            own[j] = (i < Lprev) ? ld_hint(Dr + (i - L), pol.tab) : ld_hint(Sr + slot_of(i, a.nslots), pol.tab);
+            rh[j] = (h >= L && h < Lprev) ? ld_hint(Dr + (h - L), pol.tab)
+                                          : ld_hint(Sr + slot_of(h, a.nslots), pol.tab);
           }
         }
-        if (lose) reserve(Dn, Sn, a.nslots, Ln, L, h, i + 1u);
-        const unsigned mask = __ballot_sync(kFull, lose);
-        if (mask) {
-          const int leader = __ffs(mask) - 1;
-          uint32_t wbase = 0;
-          if ((int)lane == leader) wbase = atomicAdd(&s_lcount, (uint32_t)__popc(mask));
-          wbase = __shfl_sync(kFull, wbase, leader);
-          if (lose) {
-            const uint32_t idx = wbase + __popc(mask & ((1u << lane) - 1u));
-            if (idx < kLoserBuf) {
-              s_lbuf[idx] = i;
-            } else {  // staging full: direct append
-              const uint32_t q = atomicAdd(cnt_out, 1u);
-              if (q < a.kmax) stcg(Qout + q, i);
-              else set_status(&ctrl->status, PIP_EINTERNAL);
+        bool win[kU];
+        Elem x[kU], y[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+          const uint32_t i = ii[j];
+          // own location free: exact window word unset, or every swap mapping to
+          // the slot of i has a priority at most i+1 (so none targets i)
+          const bool own_free = (i < Lprev) ? (own[j] == 0u) : (own[j] <= i + 1u);
+          win[j] = act[j] && own_free && rh[j] == i + 1u;
+          if (win[j]) {
+            x[j] = ld_hint(A + ii[j], pol.arr);
+            y[j] = ld_hint(A + hh[j], pol.arr);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+          if (win[j]) {
+            st_hint(A + ii[j], y[j], pol.arr_st);
+            st_hint(A + hh[j], x[j], pol.arr_st);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+          const bool lose = act[j] && !win[j];
+          if (lose) reserve(Dn, Sn, a.nslots, Ln, L, hh[j], ii[j] + 1u, pol.tab);
+          const unsigned mask = __ballot_sync(kFull, lose);
+          if (mask) {
+            const int leader = __ffs(mask) - 1;
+            uint32_t wbase = 0;
+            if ((int)lane == leader) wbase = atomicAdd(&s_lcount, (uint32_t)__popc(mask));
+            wbase = __shfl_sync(kFull, wbase, leader);
+            if (lose) {
+              const uint32_t idx = wbase + __popc(mask & ((1u << lane) - 1u));
+              if (idx < kLoserBuf) {
+                s_lbuf[idx] = ii[j];
+              } else {  // staging full: direct append
+                const uint32_t q = atomicAdd(cnt_out, 1u);
+                if (q < a.kmax) st_hint(Qout + q, ii[j], pol.tab);
+                else set_status(&ctrl->status, PIP_EINTERNAL);
+              }
             }
           }
         }
@@ -190,17 +271,17 @@ __global__ void __launch_bounds__(1024) rounds_kernel(const GridArgs a) {
       }
       __syncthreads();
       if (s_base + s_flush <= a.kmax) {
-        for (uint32_t j = threadIdx.x; j < s_flush; j += blockDim.x) stcg(Qout + s_base + j, s_lbuf[j]);
+        for (uint32_t j = threadIdx.x; j < s_flush; j += blockDim.x) st_hint(Qout + s_base + j, s_lbuf[j], pol.tab);
       } else if (threadIdx.x == 0) {
         set_status(&ctrl->status, PIP_EINTERNAL);  // cannot happen: some swap commits every round
       }
 
       // ---- (b) fresh block of round r+1 reserves
-      reserve_fresh<kExplicit>(a, Ln, L, Dn, Sn, tid, T);
+      reserve_fresh<Elem, kExplicit>(a, Ln, L, Dn, Sn, tid, T, pol.tab);
 
       // ---- (c) clean round r-1's tables (they become round r+2's)
-      clear_words(a.S[b2], a.nslots, tid, T);
-      clear_words(a.D[b2], a.F, tid, T);
+      clear_words(a.S[b2], a.nslots, tid, T, pol.tab);
+      clear_words(a.D[b2], a.F, tid, T, pol.tab);
 
       if (!grid_barrier(&ctrl->barrier, gridDim.x, epoch, &ctrl->status, a.timeout_ns)) goto done;
 
@@ -263,13 +344,24 @@ const void* select_kernel(uint32_t elem_bytes, bool explicit_h) {
 }  // namespace
 
 uint32_t* error_latch_ptr() {
-  // the symbol's device address, looked up for the current device
-  void* p = nullptr;
-  if (cudaGetSymbolAddress(&p, g_error_latch) != cudaSuccess) {
+  // the symbol's device address, looked up once per device
+  static std::mutex mu;
+  static uint32_t* cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
     return nullptr;
   }
-  return static_cast<uint32_t*>(p);
+  std::lock_guard<std::mutex> lk(mu);
+  if (cached[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_error_latch) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cached[dev] = static_cast<uint32_t*>(p);
+  }
+  return cached[dev];
 }
 
 pip_status take_error_latch(uint32_t* value) {
@@ -285,12 +377,25 @@ uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t t
   if (k == nullptr) return 0;
   DeviceInfo di;
   if (device_info(&di) != PIP_OK) return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)threads, 0) != cudaSuccess) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return (uint32_t)per_sm * (uint32_t)di.sms;
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, uint32_t>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(dev, k, threads);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)threads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    it = cache.emplace(key, per_sm).first;
+  }
+  return (uint32_t)it->second * (uint32_t)di.sms;
 }
 
 pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
@@ -331,6 +436,10 @@ pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint
   const uint32_t maxb = grid_driver_max_blocks(plan.elem_bytes, H != nullptr, plan.threads);
   if (maxb == 0) return PIP_ECUDA;
   blocks = std::max(1u, std::min(blocks, maxb));
+  if (const char* e = std::getenv("PIP_L2_FETCH_BYTES")) {
+    cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)std::atoi(e));
+    cudaGetLastError();
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(plan.threads);

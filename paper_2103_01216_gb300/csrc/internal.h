@@ -19,7 +19,12 @@ struct Ctrl {
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is one 256-byte line pair");
 
+enum Driver : uint32_t { kDriverGrid = 0, kDriverCta = 1 };
+
 struct Plan {
+  uint32_t driver = kDriverGrid;
+  uint32_t sigma = 4;
+  uint64_t smem_bytes = 0;  // on-chip scratch of the block-resident driver
   uint32_t n = 0;
   uint32_t elem_bytes = 0;
   double eps = 0.5;
@@ -60,6 +65,55 @@ struct GridArgs {
   uint64_t deadline_ns;  // whole-kernel time limit
 };
 
+// One array of a block-resident (batched) run.  40 bytes.
+struct BatchJob {
+  void* A;
+  const uint32_t* H;   // explicit targets or nullptr
+  uint64_t seed;
+  uint32_t n;
+  uint32_t F;          // fresh swaps per round for this array
+  uint32_t slot;       // index of the array in the caller's list (stats)
+  uint32_t pad;
+};
+static_assert(sizeof(BatchJob) == 40, "job layout");
+
+// Device-resident header in front of the job list.  `next` and `status` are
+// reset before every run (a 256-byte memset of the header's first line).
+struct BatchHeader {
+  uint32_t next;        // work counter: next job to take
+  uint32_t status;      // first error of the run
+  uint32_t count;
+  uint32_t fmax;
+  uint32_t sigma;
+  uint32_t pad0;
+  uint64_t deadline_ns;
+  uint32_t* latch;
+  uint32_t pad[54];
+};
+static_assert(sizeof(BatchHeader) == 256, "header is 256 bytes");
+
+struct BatchLaunch {
+  BatchHeader* hdr;
+  BatchJob* jobs;
+  pip_job_stats* stats;
+  uint32_t count;
+  uint32_t elem_bytes;
+  uint32_t fmax;
+  uint32_t sigma;
+  uint32_t threads;
+  uint32_t max_blocks;
+  bool any_explicit;
+};
+
+// Block-resident driver (cta_driver.cu).
+uint64_t cta_smem_bytes(uint32_t fmax, uint32_t sigma);
+uint32_t cta_max_fmax(uint32_t sigma);
+pip_status launch_cta_driver(const BatchLaunch& bl, cudaStream_t stream);
+// One array on one block (small prefixes): validation (explicit targets) and
+// the kernel, on `stream`; `aux` holds the 256-byte Ctrl block.
+pip_status launch_cta_single(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
+                             pip_stats* stats, cudaStream_t stream);
+
 // Device facts cached per device.
 struct DeviceInfo {
   int sms = 0;
@@ -70,6 +124,11 @@ pip_status device_info(DeviceInfo* out);
 
 // Planner (planner.cpp).
 pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options* opt, Plan* out);
+// Fresh-per-round F of one array run by the block-resident driver, within the
+// aux bound and the shared-memory cap.
+uint32_t cta_fresh(uint64_t n, double eps, const pip_options* opt, uint32_t sigma, uint32_t fcap);
+// Bytes the block-resident driver holds for one array with fresh block F.
+uint64_t cta_job_bytes(uint32_t F, uint32_t sigma);
 uint32_t elem_bytes_of(pip_dtype dtype);
 
 // Round driver launch (grid_driver.cu).  Queues the explicit-target

@@ -27,13 +27,17 @@ constexpr uint32_t kItemsPerThread = 2;  // target positions per thread per roun
 
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-uint32_t kmax_of(uint32_t F) { return F + (F + 3) / 4; }  // room for ~25% carried losers
+// Cap on the active set: the fresh block F plus room for 1.5 F carried
+// losers, so the throttle in the driver leaves F untouched unless losers pile
+// up (they are typically a few percent).  Only the used part of the loser
+// queues is ever touched.
+uint32_t kmax_of(uint32_t F) { return (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, (uint64_t)F * 5 / 2 + 2); }
 
 // Fills the layout fields for a given F and slot factor; returns aux bytes.
 uint64_t layout(Plan* p, uint32_t F, uint32_t slot_factor) {
   p->F = F;
   p->kmax = kmax_of(F);
-  const uint64_t ns = (uint64_t)slot_factor * p->kmax;
+  const uint64_t ns = (uint64_t)slot_factor * p->F + 32;
   p->nslots = (uint32_t)std::min<uint64_t>(ns, 0xFFFFFFF0ull);
   uint64_t off = align_up(sizeof(Ctrl));
   for (int j = 0; j < 3; ++j) {
@@ -92,6 +96,24 @@ uint32_t elem_bytes_of(pip_dtype dtype) {
   }
 }
 
+uint64_t cta_job_bytes(uint32_t F, uint32_t sigma) { return cta_smem_bytes(F, sigma); }
+
+uint32_t cta_fresh(uint64_t n, double eps, const pip_options* opt, uint32_t sigma, uint32_t fcap) {
+  if (n < 2) return 1;
+  pip_options o{};
+  if (opt != nullptr) o = *opt;
+  const double x = std::pow((double)n, 1.0 - eps);
+  const uint64_t bound = (uint64_t)std::floor(PIP_AUX_C * x) + 4096;
+  double want;
+  if (o.fresh_per_round) want = (double)o.fresh_per_round;
+  else want = (o.prefix_c > 0.0 ? o.prefix_c : kDefaultPrefixC) * x;
+  uint64_t F = (uint64_t)std::max(1.0, std::ceil(want));
+  F = std::min<uint64_t>({F, n - 1, (uint64_t)std::max(1u, fcap)});
+  // device bytes (the 256-byte control block) plus shared memory stay in the bound
+  while (F > 1 && sizeof(Ctrl) + cta_job_bytes((uint32_t)F, sigma) > bound) --F;
+  return (uint32_t)F;
+}
+
 pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options* opt, Plan* out) {
   const uint32_t eb = elem_bytes_of(dtype);
   if (eb == 0 || !(eps > 0.0 && eps < 1.0) || n >= (1ull << 32) || n < 2) return PIP_EINVAL;
@@ -109,7 +131,7 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
   uint32_t slot_factor = o.slot_factor ? o.slot_factor : kDefaultSlotFactor;
   if (slot_factor < 2 || slot_factor > 16) return PIP_EINVAL;
   uint32_t threads = o.block_threads ? o.block_threads : kDefaultThreads;
-  if (threads < 128 || threads > 1024 || threads % 32 != 0) return PIP_EINVAL;
+  if (threads < 128 || threads > 512 || threads % 32 != 0) return PIP_EINVAL;
   p.threads = threads;
 
   // requested prefix
@@ -122,13 +144,13 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
   }
   uint64_t F = (uint64_t)std::max(1.0, std::ceil(want));
   F = std::min<uint64_t>(F, n - 1);
-  // the hot tables (the one read and the one reserved into each round) stay
-  // within half of L2 unless the caller fixed F explicitly
+  // the three slot tables (read, reserved into, being cleared) stay within
+  // half of L2 unless the caller fixed F explicitly
   DeviceInfo di;
   const bool have_dev = device_info(&di) == PIP_OK;
   if (!o.fresh_per_round && !(o.prefix_c > 0.0) && have_dev && di.l2_bytes > 0) {
-    const uint64_t hot_cap = di.l2_bytes / 2;
-    const uint64_t per_F = 2ull * 4ull * slot_factor * 5ull / 4ull;  // 2 tables * 4 B * slots per F
+    const uint64_t hot_cap = di.l2_bytes * 2 / 5;
+    const uint64_t per_F = 3ull * 4ull * slot_factor;  // 3 slot tables * 4 B * slots per F
     F = std::max<uint64_t>(1, std::min<uint64_t>(F, hot_cap / per_F));
   }
   // shrink until the scratch obeys the bound
@@ -138,6 +160,31 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
     F = std::max<uint64_t>(1, std::min<uint64_t>(nf, F - 1));
   }
   if (p.aux_bytes > p.aux_bound) return PIP_EINVAL;  // cannot happen for n >= 2: F=1 needs ~2.3 KB
+
+  p.sigma = slot_factor;
+  // one block with shared-memory tables when the prefix fits there (forced
+  // either way by the flags)
+  const uint32_t fcap = cta_max_fmax(slot_factor);
+  const bool want_cta = (o.flags & PIP_FLAG_FORCE_CTA) || (!(o.flags & PIP_FLAG_FORCE_GRID) && F <= fcap);
+  if (want_cta) {
+    p.driver = kDriverCta;
+    p.F = cta_fresh(n, eps, opt, slot_factor, fcap);
+    p.kmax = p.F * 5 / 2 + 2;
+    p.nslots = slot_factor * p.F + 32;
+    p.smem_bytes = cta_job_bytes(p.F, slot_factor);
+    p.aux_bytes = sizeof(Ctrl);
+    p.blocks = 1;
+    p.threads = o.block_threads ? threads : 1024;
+    uint64_t tmo = o.wait_timeout_ns ? o.wait_timeout_ns : kDefaultTimeoutNs;
+    p.timeout_ns = tmo;
+    p.deadline_ns = 60000000000ull + 5000ull * (p.n / p.F + 1) + 20ull * p.n;
+    if (const char* e = std::getenv("PIP_DEADLINE_MS")) {
+      const long long ms = std::atoll(e);
+      if (ms > 0) p.deadline_ns = (uint64_t)ms * 1000000ull;
+    }
+    *out = p;
+    return PIP_OK;
+  }
 
   // grid: enough threads for ~kItemsPerThread active swaps each, at most what
   // can be co-resident (a cooperative launch needs every block resident)

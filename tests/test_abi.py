@@ -73,12 +73,23 @@ def test_plan_obeys_the_aux_bound(pip, dtype, eps, n):
     p = pip.plan(n, dtype, eps)
     x = n ** (1.0 - eps)
     assert p["aux_bound_bytes"] == math.floor(pip.AUX_C * x) + 4096
-    assert p["aux_bytes"] <= p["aux_bound_bytes"]
+    assert p["aux_bytes"] + p["smem_bytes"] <= p["aux_bound_bytes"]
     assert 1 <= p["fresh_per_round"] <= n - 1
+    assert p["driver"] in (pip.DRIVER_GRID, pip.DRIVER_CTA)
     assert p["max_active"] >= p["fresh_per_round"]
-    assert p["slots"] >= 2 * p["max_active"]
+    assert p["slots"] >= 2 * p["fresh_per_round"]
     assert p["min_rounds"] == -(-(n - 1) // p["fresh_per_round"])
     assert pip.aux_bytes(n, dtype, eps) == p["aux_bytes"]
+
+
+def test_driver_selection(pip):
+    # small prefixes run on one block with shared-memory tables, large ones on the grid
+    assert pip.plan(1 << 20, "u64", 0.5)["driver"] == pip.DRIVER_CTA
+    assert pip.plan(10**9, "u64", 0.75)["driver"] == pip.DRIVER_CTA
+    assert pip.plan(10**9, "u64", 0.25)["driver"] == pip.DRIVER_GRID
+    assert pip.plan(1 << 20, "u64", 0.5, flags=pip.FLAG_FORCE_GRID)["driver"] == pip.DRIVER_GRID
+    p = pip.plan(10**9, "u64", 0.25, flags=pip.FLAG_FORCE_CTA)
+    assert p["driver"] == pip.DRIVER_CTA and p["smem_bytes"] <= 227 * 1024
 
 
 def test_plan_prefix_tracks_n_to_the_one_minus_eps(pip):
@@ -91,10 +102,29 @@ def test_plan_prefix_tracks_n_to_the_one_minus_eps(pip):
 
 
 def test_plan_overrides(pip):
-    p = pip.plan(1 << 20, "u64", 0.5, fresh_per_round=7, slot_factor=8, grid_blocks=3, block_threads=256)
-    assert p["fresh_per_round"] == 7 and p["slots"] == 8 * p["max_active"]
+    p = pip.plan(1 << 20, "u64", 0.5, fresh_per_round=7, slot_factor=8, grid_blocks=3, block_threads=256,
+                 flags=pip.FLAG_FORCE_GRID)
+    assert p["fresh_per_round"] == 7 and p["slots"] == 8 * 7 + 32
     assert p["grid_blocks"] == 3 and p["block_threads"] == 256
     with pytest.raises(pip.PipError):
         pip.plan(1 << 20, "u64", 0.5, slot_factor=1)
     with pytest.raises(pip.PipError):
         pip.plan(1 << 20, "u64", 0.5, block_threads=100)
+
+
+def test_batch_plan_host_only(pip):
+    items = (pip.BatchItem * 3)()
+    for j, n in enumerate([300, 1 << 16, 1 << 22]):
+        items[j].A_dev = 256 * (j + 1)
+        items[j].n = n
+        items[j].seed = j
+    plan = pip.BatchPlan()
+    assert pip.lib().pip_batch_plan_make(items, 3, pip.U32, 0.5, None, ctypes.byref(plan)) == 0
+    assert plan.count == 3 and plan.total_elems == 300 + (1 << 16) + (1 << 22)
+    assert 1 <= plan.fmax <= 2 * 2048 + 1
+    assert plan.jobs_bytes == 256 + 3 * 40
+    # per-array scratch (shared memory) stays within that array's bound
+    x = (1 << 22) ** 0.5
+    assert plan.smem_bytes + 256 <= pip.AUX_C * x + 4096
+    items[1].n = 1 << 32
+    assert pip.lib().pip_batch_plan_make(items, 3, pip.U32, 0.5, None, ctypes.byref(plan)) == pip.PIP_EINVAL

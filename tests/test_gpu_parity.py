@@ -24,6 +24,10 @@ def pip():
     return load_pip()
 
 
+# both round drivers: the persistent grid and the one-block shared-memory driver
+DRIVERS = {"grid": 32, "cta": 64}
+
+
 def expect_hashed(arr, seed):
     out = arr.copy()
     oracle.knuth_hash(out, seed)
@@ -37,25 +41,28 @@ def expect_explicit(arr, H):
 
 
 # ------------------------------------------------------------------ explicit targets
+@pytest.mark.parametrize("driver", sorted(DRIVERS))
 @pytest.mark.parametrize("F", [1, 2, 3, 8])
-def test_figure3_worked_example(pip, F):
+def test_figure3_worked_example(pip, F, driver):
     g = read_golden("fig3_worked_example.txt")
     H = np.array([int(x) for x in g["h_zero_based"].split()], dtype=np.uint32)
     expected = [int(x) for x in g["expected_output_zero_based"].split()]
     for dt in ("u32", "u64"):
-        out, stats = gpu_shuffle(pip, workloads.iota(8, dt), H=H, fresh_per_round=F, with_stats=True)
+        out, stats = gpu_shuffle(pip, workloads.iota(8, dt), H=H, fresh_per_round=F, with_stats=True,
+                                 flags=DRIVERS[driver])
         assert out.tolist() == expected
         assert stats.status == 0
         assert stats.attempts == 7 + stats.losers
 
 
+@pytest.mark.parametrize("driver", sorted(DRIVERS))
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
-def test_every_target_sequence_small_n(pip, n):
+def test_every_target_sequence_small_n(pip, n, driver):
     for F in sorted({1, 2, n - 1}):
         for Ht in itertools.product(*[range(i + 1) for i in range(n)]):
             H = np.array(Ht, dtype=np.uint32)
             arr = workloads.iota(n, "u64")
-            out, _ = gpu_shuffle(pip, arr, H=H, fresh_per_round=F)
+            out, _ = gpu_shuffle(pip, arr, H=H, fresh_per_round=F, flags=DRIVERS[driver])
             assert np.array_equal(out, expect_explicit(arr, H)), (F, Ht)
 
 
@@ -80,12 +87,13 @@ def closed_form_targets(n):
     }
 
 
+@pytest.mark.parametrize("driver", sorted(DRIVERS))
 @pytest.mark.parametrize("n", [2, 3, 1000, 20011])
-@pytest.mark.parametrize("F", [1, 7, 4096])
-def test_closed_form_worst_cases(pip, n, F):
+@pytest.mark.parametrize("F", [1, 7, 3000])
+def test_closed_form_worst_cases(pip, n, F, driver):
     for name, H in closed_form_targets(n).items():
         arr = workloads.iota(n, "u64")
-        out, stats = gpu_shuffle(pip, arr, H=H, fresh_per_round=F, with_stats=True)
+        out, stats = gpu_shuffle(pip, arr, H=H, fresh_per_round=F, with_stats=True, flags=DRIVERS[driver])
         if name == "zero":
             assert out.tolist() == [(i + 1) % n for i in range(n)]
             assert stats.rounds == n - 1  # depth n-1 chain: exactly one commit per round
@@ -107,34 +115,39 @@ def test_sattolo_targets(pip, n):
     assert np.array_equal(out, expect_explicit(arr, H))
 
 
-@pytest.mark.parametrize("n,F", [(1000, 1), (1000, 64), (65537, 256), (300007, 4096), (1 << 20, 100000)])
-def test_random_explicit_targets(pip, n, F):
+@pytest.mark.parametrize("driver", sorted(DRIVERS))
+@pytest.mark.parametrize("n,F", [(1000, 1), (1000, 64), (65537, 256), (300007, 3000), (1 << 20, 100000)])
+def test_random_explicit_targets(pip, n, F, driver):
+    if driver == "cta" and F > 3000:
+        pytest.skip("prefix larger than one block's shared memory")
     H = workloads.random_targets(n, rng_seed=n + F)
     arr = workloads.iota(n, "u64")
-    out, stats = gpu_shuffle(pip, arr, H=H, fresh_per_round=F, with_stats=True)
+    out, stats = gpu_shuffle(pip, arr, H=H, fresh_per_round=F, with_stats=True, flags=DRIVERS[driver])
     assert np.array_equal(out, expect_explicit(arr, H))
     assert stats.rounds >= -(-(n - 1) // F)
     assert stats.attempts == (n - 1) + stats.losers
 
 
 # ------------------------------------------------------------------ hashed targets
-def test_config_2pow20_u64_seed1_eps_half(pip):
+@pytest.mark.parametrize("driver", sorted(DRIVERS))
+def test_config_2pow20_u64_seed1_eps_half(pip, driver):
     n = 1 << 20
     arr = workloads.iota(n, "u64")
-    out, stats = gpu_shuffle(pip, arr, seed=1, eps=0.5, with_stats=True)
+    out, stats = gpu_shuffle(pip, arr, seed=1, eps=0.5, with_stats=True, flags=DRIVERS[driver])
     assert np.array_equal(out, expect_hashed(arr, 1))
     assert stats.status == 0 and stats.attempts == (n - 1) + stats.losers
-    p = pip.plan(n, "u64", 0.5)
+    p = pip.plan(n, "u64", 0.5, flags=DRIVERS[driver])
     assert stats.rounds >= p["min_rounds"]
     assert stats.max_active <= p["max_active"]
 
 
+@pytest.mark.parametrize("driver", sorted(DRIVERS))
 @pytest.mark.parametrize("n", [2, 3, 31, 32, 33, 1023, 1025, 4097, 100003])
 @pytest.mark.parametrize("dtype", ["u32", "u64", "rec128"])
-def test_ragged_sizes_all_dtypes(pip, n, dtype):
+def test_ragged_sizes_all_dtypes(pip, n, dtype, driver):
     arr = workloads.make(n, dtype)
     seed = 1000 + n
-    out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5)
+    out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5, flags=DRIVERS[driver])
     assert np.array_equal(out, expect_hashed(arr, seed))
 
 
@@ -159,9 +172,15 @@ def test_output_does_not_depend_on_launch_shape(pip):
         dict(fresh_per_round=1000, slot_factor=16),
         dict(fresh_per_round=50000, grid_blocks=1),
         dict(fresh_per_round=50000, grid_blocks=2, block_threads=128),
-        dict(fresh_per_round=50000, block_threads=1024),
+        dict(fresh_per_round=50000, block_threads=256),
         dict(fresh_per_round=n - 1),
         dict(prefix_c=0.01),
+        dict(fresh_per_round=4096, flags=2),
+        dict(flags=2),
+        dict(flags=DRIVERS["cta"]),
+        dict(flags=DRIVERS["cta"], fresh_per_round=17, slot_factor=2),
+        dict(flags=DRIVERS["cta"], fresh_per_round=3000, slot_factor=8, block_threads=256),
+        dict(flags=DRIVERS["grid"], fresh_per_round=3000),
     ]
     for c in configs:
         out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5, **c)
@@ -221,7 +240,7 @@ def test_barrier_wait_runs_out_and_reports_timeout(pip):
     n = 1 << 16
     arr = workloads.iota(n, "u64")
     A = to_dev(arr)
-    pip.shuffle(A, seed=1, eps=0.5, grid_blocks=4, flags=pip.FLAG_TEST_SKIP_BARRIER,
+    pip.shuffle(A, seed=1, eps=0.5, grid_blocks=4, flags=pip.FLAG_TEST_SKIP_BARRIER | pip.FLAG_FORCE_GRID,
                 wait_timeout_ns=50_000_000)
     with pytest.raises(pip.PipError) as e:
         pip.check()
@@ -237,12 +256,14 @@ def test_caller_provided_scratch(pip):
 
     n = 1 << 18
     arr = workloads.iota(n, "u32")
-    p = pip.plan(n, "u32", 0.5)
-    aux = torch.empty(p["aux_bytes"], dtype=torch.uint8, device="cuda")
-    A = to_dev(arr)
-    pip.shuffle(A, seed=9, eps=0.5, aux=aux)
-    pip.check()
-    assert np.array_equal(from_dev(A, arr), expect_hashed(arr, 9))
+    for flags in (DRIVERS["grid"], DRIVERS["cta"]):
+        p = pip.plan(n, "u32", 0.5, flags=flags)
+        aux = torch.empty(p["aux_bytes"], dtype=torch.uint8, device="cuda")
+        A = to_dev(arr)
+        pip.shuffle(A, seed=9, eps=0.5, aux=aux, flags=flags)
+        pip.check()
+        assert np.array_equal(from_dev(A, arr), expect_hashed(arr, 9))
+    p = pip.plan(n, "u32", 0.5, flags=DRIVERS["grid"])
     small = torch.empty(p["aux_bytes"] - 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(pip.PipError):
-        pip.shuffle(A, seed=9, eps=0.5, aux=small)
+        pip.shuffle(A, seed=9, eps=0.5, aux=small, flags=DRIVERS["grid"])
