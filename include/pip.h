@@ -56,7 +56,8 @@ typedef enum {
     PIP_ETIMEOUT = 4,  /* a bounded device-side wait ran out; the array content is unspecified */
     PIP_EAGAIN = 5,    /* serve poll: the request has not finished yet */
     PIP_EBUSY = 6,     /* serve: the request is queued behind the memory budget */
-    PIP_EINTERNAL = 7  /* a device-side consistency check failed (round cap exceeded) */
+    PIP_EINTERNAL = 7, /* a device-side consistency check failed (round cap exceeded) */
+    PIP_ETOOLARGE = 8  /* pip_shuffle_noalloc: the plan needs more scratch than the fixed area */
 } pip_status;
 
 /* Planned execution of one shuffle (filled by pip_plan). */
@@ -244,6 +245,29 @@ uint64_t pip_aux_bytes(uint64_t n, pip_dtype dtype, double eps);
  * the stream reported a CUDA error.
  */
 pip_status pip_check(void *stream);
+
+/*
+ * pip_shuffle_noalloc -- pip_shuffle for callers that cannot allocate device
+ * memory at call time (an application that reserved the whole GPU for its
+ * own pool, a latency-critical path that must not enter the CUDA allocator,
+ * code holding a lock the allocator may need).  The paper has no counterpart:
+ * it is an interface for such callers, not part of the method.
+ *   Same arguments, same result as pip_shuffle (hashed targets, persistent
+ *   grid driver), but the scratch comes from a fixed 16 MiB device area
+ *   compiled into the library, which every GPU that loads the library keeps
+ *   until the process exits.  Nothing is allocated or freed.
+ *   Requests whose plan needs more than 16 MiB of scratch (pip_plan with
+ *   PIP_FLAG_FORCE_GRID reports the need as aux_bytes) return PIP_ETOOLARGE
+ *   before anything is queued.
+ *   The first call on a device looks up the area's device address (and may
+ *   load the library's device code): make it before any stream capture.
+ *   Each call clears the part of the area it uses; the area keeps the last
+ *   call's contents.  All calls on a device share the area, so calls whose
+ *   work overlaps on the GPU race and corrupt each other: order them on one
+ *   stream.
+ */
+pip_status pip_shuffle_noalloc(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed,
+                               double eps, void *stream);
 
 /* pip_status_string -- static English description of a status code. */
 const char *pip_status_string(pip_status s);

@@ -34,8 +34,9 @@ STATUS = {
     5: "PIP_EAGAIN",
     6: "PIP_EBUSY",
     7: "PIP_EINTERNAL",
+    8: "PIP_ETOOLARGE",
 }
-PIP_OK, PIP_EINVAL, PIP_ENOMEM, PIP_ECUDA, PIP_ETIMEOUT, PIP_EAGAIN, PIP_EBUSY, PIP_EINTERNAL = range(8)
+PIP_OK, PIP_EINVAL, PIP_ENOMEM, PIP_ECUDA, PIP_ETIMEOUT, PIP_EAGAIN, PIP_EBUSY, PIP_EINTERNAL, PIP_ETOOLARGE = range(9)
 FLAG_TEST_SKIP_BARRIER = 1
 FLAG_PREFETCH = 2
 AUX_C = 128.0
@@ -180,6 +181,8 @@ def lib() -> ctypes.CDLL:
         L.pip_batch_prepare.restype = i32
         L.pip_batch_run.argtypes = [ctypes.POINTER(BatchPlan), vp, vp, vp]
         L.pip_batch_run.restype = i32
+        L.pip_shuffle_noalloc.argtypes = [vp, u64, i32, u64, dbl, vp]
+        L.pip_shuffle_noalloc.restype = i32
         _lib = L
         return L
 

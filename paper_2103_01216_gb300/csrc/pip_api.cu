@@ -246,6 +246,7 @@ const char* pip_status_string(pip_status s) {
     case PIP_EAGAIN: return "not finished yet";
     case PIP_EBUSY: return "queued behind the memory budget";
     case PIP_EINTERNAL: return "internal consistency check failed";
+    case PIP_ETOOLARGE: return "needs more scratch than the fixed no-allocation area holds";
     default: return "unknown status";
   }
 }
