@@ -227,6 +227,101 @@ pip_status pip_batch_prepare(const pip_batch_item *items, const pip_batch_plan *
 pip_status pip_batch_run(const pip_batch_plan *plan, void *jobs_dev, pip_job_stats *stats_dev,
                          void *stream);
 
+/* ------------------------------------------------------------------ serving */
+
+/* A request server (opaque). */
+typedef struct pip_server pip_server;
+
+/* Server tuning; zero fields keep the defaults. */
+typedef struct {
+    uint32_t max_resident;     /* requests on the device at once (default 1024) */
+    uint32_t rounds_per_tick;  /* rounds each resident request advances per tick (default 128) */
+    uint32_t fresh_cap;        /* cap on a request's fresh block F (default 1024; one block each) */
+    uint32_t slot_factor;      /* reservation slots per fresh swap (default 4) */
+    uint32_t block_threads;    /* threads per block of the tick kernel (default 512) */
+    uint32_t pad;
+    double prefix_c;           /* C in F = C * n^(1-eps) (default 1) */
+} pip_serve_options;
+
+/* Per-request record.  Times are host steady-clock nanoseconds. */
+typedef struct {
+    uint32_t status;
+    uint32_t rounds;
+    uint64_t attempts;
+    uint64_t losers;
+    uint64_t n;
+    uint64_t charged_bytes;    /* array + scratch charged against the budget */
+    int64_t submit_ns;
+    int64_t admit_ns;
+    int64_t done_ns;
+    uint32_t ticks;            /* ticks the request was resident for */
+    uint32_t fresh_per_round;
+} pip_req_stats;
+
+/* Server-wide counters. */
+typedef struct {
+    uint64_t budget_bytes;
+    uint64_t used_bytes;
+    uint64_t peak_used_bytes;  /* never above budget_bytes */
+    uint64_t submitted;
+    uint64_t admitted;
+    uint64_t completed;
+    uint64_t ticks;
+    uint32_t resident;
+    uint32_t waiting;
+    uint32_t tick_blocks;
+    uint32_t fresh_cap;
+    uint32_t status;           /* PIP_ECUDA once a tick failed */
+    uint32_t pad;
+} pip_serve_info;
+
+/*
+ * pip_serve_create -- starts a server on `device` with a device-memory budget.
+ * A background thread repeats ticks: it admits waiting requests in arrival
+ * order while budget_bytes allows, charging each request its array
+ * (n * element bytes) plus its O(n^(1-eps)) scratch; it then advances every
+ * resident request by up to rounds_per_tick rounds in one launch (each
+ * request on one block, round state kept in device memory between ticks),
+ * and retires finished ones.  Requests arriving meanwhile join at the next
+ * tick, so their work overlaps on the device with the requests already
+ * running (continuous batching).  The result of every request equals
+ * pip_shuffle on the same array, seed and eps.
+ */
+pip_status pip_serve_create(pip_server **out, uint64_t device_budget_bytes, int device,
+                            const pip_serve_options *opt);
+
+/*
+ * pip_serve_submit -- queues a request; never blocks on the GPU.
+ *   A_dev: the caller's device array (caller-owned, must stay valid until the
+ *          request is released), or NULL: the server allocates the array when
+ *          the request is admitted and fills it with A[i] = i (16-byte
+ *          records: {i, splitmix64(i)}).
+ *   ticket: filled with the request's handle.
+ * PIP_EINVAL if the request alone exceeds the budget.
+ */
+pip_status pip_serve_submit(pip_server *srv, void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed,
+                            double eps, uint64_t *ticket);
+
+/* pip_serve_poll -- PIP_EAGAIN while the request runs; once done, its status
+ * (PIP_OK on success), the array pointer and the stats (both optional). */
+pip_status pip_serve_poll(pip_server *srv, uint64_t ticket, void **A_out, pip_req_stats *st);
+
+/* pip_serve_wait -- pip_serve_poll that blocks up to timeout_ms. */
+pip_status pip_serve_wait(pip_server *srv, uint64_t ticket, uint32_t timeout_ms, void **A_out,
+                          pip_req_stats *st);
+
+/* pip_serve_release -- forgets a finished request, frees its array if the
+ * server allocated it, and returns its charge to the budget. PIP_EAGAIN if
+ * the request has not finished. */
+pip_status pip_serve_release(pip_server *srv, uint64_t ticket);
+
+/* pip_serve_info_get -- server counters. */
+pip_status pip_serve_info_get(pip_server *srv, pip_serve_info *out);
+
+/* pip_serve_destroy -- drops never-admitted requests, lets resident ones
+ * finish, frees everything the server owns. */
+pip_status pip_serve_destroy(pip_server *srv);
+
 /*
  * pip_plan -- the plan pip_shuffle_ex would use for these arguments on the
  * current device (host only; queries device attributes, launches nothing).

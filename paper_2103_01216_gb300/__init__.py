@@ -128,6 +128,52 @@ class Stats(ctypes.Structure):
     ]
 
 
+class ServeOptions(ctypes.Structure):
+    _fields_ = [
+        ("max_resident", ctypes.c_uint32),
+        ("rounds_per_tick", ctypes.c_uint32),
+        ("fresh_cap", ctypes.c_uint32),
+        ("slot_factor", ctypes.c_uint32),
+        ("block_threads", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+        ("prefix_c", ctypes.c_double),
+    ]
+
+
+class ReqStats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_uint32),
+        ("rounds", ctypes.c_uint32),
+        ("attempts", ctypes.c_uint64),
+        ("losers", ctypes.c_uint64),
+        ("n", ctypes.c_uint64),
+        ("charged_bytes", ctypes.c_uint64),
+        ("submit_ns", ctypes.c_int64),
+        ("admit_ns", ctypes.c_int64),
+        ("done_ns", ctypes.c_int64),
+        ("ticks", ctypes.c_uint32),
+        ("fresh_per_round", ctypes.c_uint32),
+    ]
+
+
+class ServeInfo(ctypes.Structure):
+    _fields_ = [
+        ("budget_bytes", ctypes.c_uint64),
+        ("used_bytes", ctypes.c_uint64),
+        ("peak_used_bytes", ctypes.c_uint64),
+        ("submitted", ctypes.c_uint64),
+        ("admitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("ticks", ctypes.c_uint64),
+        ("resident", ctypes.c_uint32),
+        ("waiting", ctypes.c_uint32),
+        ("tick_blocks", ctypes.c_uint32),
+        ("fresh_cap", ctypes.c_uint32),
+        ("status", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+    ]
+
+
 STATS_BYTES = ctypes.sizeof(Stats)
 JOB_STATS_BYTES = ctypes.sizeof(JobStats)
 DRIVER_GRID, DRIVER_CTA = 0, 1
@@ -183,6 +229,20 @@ def lib() -> ctypes.CDLL:
         L.pip_batch_run.restype = i32
         L.pip_shuffle_noalloc.argtypes = [vp, u64, i32, u64, dbl, vp]
         L.pip_shuffle_noalloc.restype = i32
+        L.pip_serve_create.argtypes = [ctypes.POINTER(vp), u64, i32, ctypes.POINTER(ServeOptions)]
+        L.pip_serve_create.restype = i32
+        L.pip_serve_submit.argtypes = [vp, vp, u64, i32, u64, dbl, ctypes.POINTER(u64)]
+        L.pip_serve_submit.restype = i32
+        L.pip_serve_poll.argtypes = [vp, u64, ctypes.POINTER(vp), ctypes.POINTER(ReqStats)]
+        L.pip_serve_poll.restype = i32
+        L.pip_serve_wait.argtypes = [vp, u64, u32, ctypes.POINTER(vp), ctypes.POINTER(ReqStats)]
+        L.pip_serve_wait.restype = i32
+        L.pip_serve_release.argtypes = [vp, u64]
+        L.pip_serve_release.restype = i32
+        L.pip_serve_info_get.argtypes = [vp, ctypes.POINTER(ServeInfo)]
+        L.pip_serve_info_get.restype = i32
+        L.pip_serve_destroy.argtypes = [vp]
+        L.pip_serve_destroy.restype = i32
         _lib = L
         return L
 
@@ -363,3 +423,89 @@ def shuffle_batch(arrays, seeds, eps: float = 0.5, stream=None) -> None:
 def read_job_stats(buf, count: int):
     raw = bytes(buf.cpu().numpy().tobytes()[: JOB_STATS_BYTES * count])
     return [JobStats.from_buffer_copy(raw, j * JOB_STATS_BYTES) for j in range(count)]
+
+
+# ---------------------------------------------------------------- serving
+_TORCH_DTYPE = {U32: "int32", U64: "int64", REC128: "int64"}
+
+
+class _DeviceArray:
+    """Zero-copy view of raw device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, dtype: int):
+        shape = (n, 2) if dtype == REC128 else (n,)
+        typestr = "<i4" if dtype == U32 else "<i8"
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def device_view(ptr: int, n: int, dtype: int | str):
+    """A torch tensor aliasing n elements of device memory at ``ptr``."""
+    import torch
+
+    d = DTYPES[dtype] if isinstance(dtype, str) else dtype
+    if n == 0 or not ptr:
+        return torch.empty((0, 2) if d == REC128 else (0,), dtype=getattr(torch, _TORCH_DTYPE[d]), device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, n, d), device="cuda")
+
+
+class Server:
+    """A request server (``pip_serve_*``): memory-budgeted admission and
+    continuous batching of shuffle requests on one GPU."""
+
+    def __init__(self, budget_bytes: int, device: int = 0, **options):
+        o = ServeOptions()
+        for k, v in options.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown server option {k}")
+            setattr(o, k, v)
+        self._h = ctypes.c_void_p()
+        _raise(lib().pip_serve_create(ctypes.byref(self._h), budget_bytes, device, ctypes.byref(o)),
+               "pip_serve_create")
+
+    def submit(self, n: int, dtype: int | str = "u64", seed: int = 0, eps: float = 0.5, A=None) -> int:
+        d = DTYPES[dtype] if isinstance(dtype, str) else dtype
+        t = ctypes.c_uint64()
+        ptr = None
+        if A is not None:
+            if tensor_dtype(A) != d or A.shape[0] != n:
+                raise ValueError("A does not match n / dtype")
+            ptr = A.data_ptr()
+        _raise(lib().pip_serve_submit(self._h, ptr, n, d, seed, eps, ctypes.byref(t)), "pip_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running; else (device pointer, ReqStats)."""
+        p, st = ctypes.c_void_p(), ReqStats()
+        rc = lib().pip_serve_poll(self._h, ticket, ctypes.byref(p), ctypes.byref(st))
+        if rc == PIP_EAGAIN:
+            return None
+        _raise(rc, "pip_serve_poll")
+        return p.value or 0, st
+
+    def wait(self, ticket: int, timeout_ms: int = 600000):
+        p, st = ctypes.c_void_p(), ReqStats()
+        rc = lib().pip_serve_wait(self._h, ticket, timeout_ms, ctypes.byref(p), ctypes.byref(st))
+        _raise(rc, "pip_serve_wait")
+        return p.value or 0, st
+
+    def release(self, ticket: int) -> None:
+        _raise(lib().pip_serve_release(self._h, ticket), "pip_serve_release")
+
+    def info(self) -> ServeInfo:
+        out = ServeInfo()
+        _raise(lib().pip_serve_info_get(self._h, ctypes.byref(out)), "pip_serve_info_get")
+        return out
+
+    def close(self) -> None:
+        if self._h:
+            rc = lib().pip_serve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            _raise(rc, "pip_serve_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False

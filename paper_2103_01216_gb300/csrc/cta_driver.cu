@@ -4,13 +4,9 @@
 // blocks pulls arrays from a job list (largest first), which is the batched
 // path: thousands of independent arrays in one launch.
 //
-// The round structure is the one of the grid driver (deterministic
-// reservations over the first unfinished swaps, Algorithm 1 under the
-// Decomposable Property, Section 4.1; RP-OneRes / RP-Final rule and dense
-// window, Appendix A.2): round r commits with the tables of round r while
-// its losers and the fresh block W_{r+1} reserve into the other buffer;
-// after a bar.sync the tables of round r are cleared (the cleaning phase of
-// Appendix A.1) and a second bar.sync opens round r+1.
+// The round loop itself (cta_rounds.cuh) follows the grid driver's structure
+// (Algorithm 1 under the Decomposable Property, Section 4.1; RP-OneRes rule
+// and RP-Final window, Appendix A.2).
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -19,166 +15,13 @@
 #include <mutex>
 #include <vector>
 
+#include "cta_rounds.cuh"
 #include "device.cuh"
 #include "internal.h"
 
 namespace pip {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename Elem>
-__device__ __forceinline__ uint32_t job_target(const BatchJob& j, uint32_t i) {
-  return j.H != nullptr ? __ldg(j.H + i) : hashed_target(j.seed, i);
-}
-
-__device__ __forceinline__ void sreserve(uint32_t* D, uint32_t* S, uint32_t ns, uint32_t wlo, uint32_t whi,
-                                         uint32_t h, uint32_t prio) {
-  if (h >= wlo && h < whi) atomicMax(D + (h - wlo), prio);
-  else atomicMax(S + slot_of(h, ns), prio);
-}
-
-__device__ __forceinline__ void sclear(uint32_t* p, uint32_t count) {
-  for (uint32_t j = threadIdx.x; j < count; j += blockDim.x) p[j] = 0u;
-}
-
-// Runs the whole shuffle of one array inside the calling block.  Returns the
-// status (0 = ok).  All control decisions are block-uniform.
-template <typename Elem>
-__device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, uint32_t sigma, uint64_t deadline_ns,
-                            uint64_t t_start, pip_job_stats* st) {
-  __shared__ uint32_t s_cnt[2];
-  __shared__ uint32_t s_abort;
-  const uint32_t n = job.n;
-  const uint32_t F = job.F;
-  const uint32_t ns = sigma * F + 32u;
-  const uint32_t kmax = F * 5u / 2u + 2u;
-  const uint32_t NS = sigma * fmax + 32u;
-  const uint32_t KMAX = fmax * 5u / 2u + 2u;
-  // buffer k of each table (k = round parity), addressed arithmetically so
-  // that nothing is indexed through a local array
-  uint32_t* const S_base = smem;
-  uint32_t* const D_base = smem + 2 * NS;
-  uint32_t* const Q_base = smem + 2 * NS + 2 * fmax;
-  Elem* A = static_cast<Elem*>(job.A);
-  const uint32_t tid = threadIdx.x, NT = blockDim.x, lane = tid & 31u;
-
-  uint32_t rounds = 0, max_active = 0;
-  uint64_t attempts = 0, losers_total = 0;
-  uint32_t status = 0;
-  if (n >= 2u) {
-    sclear(S_base, ns);
-    sclear(S_base + NS, ns);
-    sclear(D_base, F);
-    sclear(D_base + fmax, F);
-    if (tid == 0) {
-      s_cnt[0] = 0;
-      s_cnt[1] = 0;
-      s_abort = 0;
-    }
-    __syncthreads();
-    uint32_t Lprev = n;
-    uint32_t L = n - min(F, n - 1u);
-    uint32_t nl = 0;
-    uint32_t m = Lprev - L;
-    for (uint32_t i = L + tid; i < Lprev; i += NT) {
-      const uint32_t h = job_target<Elem>(job, i);
-      if (h != i) sreserve(D_base, S_base, ns, L, Lprev, h, i + 1u);
-    }
-    __syncthreads();
-    for (uint32_t r = 0;; ++r) {
-      const uint32_t b = r & 1u, nb = b ^ 1u;
-      uint32_t* const Sb = S_base + b * NS;
-      uint32_t* const Snb = S_base + nb * NS;
-      uint32_t* const Db = D_base + b * fmax;
-      uint32_t* const Dnb = D_base + nb * fmax;
-      uint32_t* const Qb = Q_base + b * KMAX;
-      uint32_t* const Qnb = Q_base + nb * KMAX;
-      uint32_t fn = min(F, L - 1u);
-      fn = min(fn, kmax - m + 1u);
-      const uint32_t Ln = L - fn;
-      // ---- commit round r
-      for (uint32_t p0 = tid & ~31u; p0 < m; p0 += NT) {
-        const uint32_t p = p0 + lane;
-        bool lose = false;
-        uint32_t i = 0, h = 0;
-        if (p < m) {
-          i = (p < nl) ? Qb[p] : L + (p - nl);
-          h = job_target<Elem>(job, i);
-          if (h != i) {
-            const uint32_t own = (i < Lprev) ? Db[i - L] : Sb[slot_of(i, ns)];
-            const uint32_t rh = (h >= L && h < Lprev) ? Db[h - L] : Sb[slot_of(h, ns)];
-            const bool own_free = (i < Lprev) ? (own == 0u) : (own <= i + 1u);
-            if (own_free && rh == i + 1u) {
-              const Elem x = ldcg(A + i);
-              const Elem y = ldcg(A + h);
-              stcg(A + i, y);
-              stcg(A + h, x);
-            } else {
-              lose = true;
-            }
-          }
-        }
-        if (lose) sreserve(Dnb, Snb, ns, Ln, L, h, i + 1u);
-        const unsigned mask = __ballot_sync(kFull, lose);
-        if (mask) {
-          const int leader = __ffs(mask) - 1;
-          uint32_t base = 0;
-          if ((int)lane == leader) base = atomicAdd(&s_cnt[nb], (uint32_t)__popc(mask));
-          base = __shfl_sync(kFull, base, leader);
-          if (lose) {
-            const uint32_t q = base + __popc(mask & ((1u << lane) - 1u));
-            if (q < kmax) Qnb[q] = i;
-            else s_abort = PIP_EINTERNAL;
-          }
-        }
-      }
-      // ---- fresh block W_{r+1} reserves
-      for (uint32_t i = Ln + tid; i < L; i += NT) {
-        const uint32_t h = job_target<Elem>(job, i);
-        if (h != i) sreserve(Dnb, Snb, ns, Ln, L, h, i + 1u);
-      }
-      __syncthreads();
-      const uint32_t nl_next = s_cnt[nb];
-      // ---- clean round r's tables; they take round r+2's reservations
-      sclear(Sb, ns);
-      sclear(Db, F);
-      if (tid == 0) {
-        s_cnt[b] = 0;
-        if (nl_next >= m) s_abort = PIP_EINTERNAL;  // no commit: impossible
-        if (globaltimer_ns() - t_start > deadline_ns) s_abort = PIP_ETIMEOUT;
-      }
-      __syncthreads();
-      rounds = r + 1u;
-      attempts += m;
-      losers_total += nl_next;
-      max_active = max(max_active, m);
-      if (s_abort != 0u) {
-        status = s_abort;
-        break;
-      }
-      Lprev = L;
-      L = Ln;
-      nl = nl_next;
-      m = nl_next + fn;
-      if (m == 0u) break;
-      if (m > kmax || rounds > n + 8u) {
-        status = PIP_EINTERNAL;
-        break;
-      }
-    }
-  }
-  if (tid == 0 && st != nullptr) {
-    st->status = status;
-    st->rounds = rounds;
-    st->attempts = attempts;
-    st->losers = losers_total;
-    st->max_active = max_active;
-  }
-  __syncthreads();  // the block's smem is reused by its next job
-  return status;
-}
 
 template <typename Elem>
 __global__ void __launch_bounds__(1024) cta_batch_kernel(const BatchHeader* hdr, const BatchJob* jobs,
@@ -197,7 +40,7 @@ __global__ void __launch_bounds__(1024) cta_batch_kernel(const BatchHeader* hdr,
     if (j >= hdr->count) break;
     const BatchJob job = jobs[j];
     const uint32_t st = run_job<Elem>(job, smem, hdr->fmax, hdr->sigma, hdr->deadline_ns, t_start,
-                                      stats != nullptr ? stats + job.slot : nullptr);
+                                      stats != nullptr ? stats + job.slot : nullptr, nullptr, 0u);
     if (st != 0u && threadIdx.x == 0) {
       set_status(&h->status, st);
       atomicCAS(hdr->latch, 0u, st);
@@ -230,7 +73,7 @@ __global__ void __launch_bounds__(1024) cta_single_kernel(const BatchJob job, ui
     }
     return;
   }
-  const uint32_t st = run_job<Elem>(job, smem, job.F, sigma, deadline_ns, globaltimer_ns(), &s_st);
+  const uint32_t st = run_job<Elem>(job, smem, job.F, sigma, deadline_ns, globaltimer_ns(), &s_st, nullptr, 0u);
   if (threadIdx.x == 0) {
     if (st != 0u) {
       set_status(&ctrl->status, st);

@@ -92,6 +92,24 @@ struct BatchHeader {
 };
 static_assert(sizeof(BatchHeader) == 256, "header is 256 bytes");
 
+// Round state of a request run in slices (serving), in device memory.  The
+// frontier and the carried losers describe the next round completely.
+struct ResumeState {
+  uint32_t started;
+  uint32_t done;
+  uint32_t status;
+  uint32_t rounds;
+  uint32_t L;          // lowest activated step
+  uint32_t Lprev;      // end of the current fresh block
+  uint32_t nl;         // carried losers (in Q)
+  uint32_t m;          // active swaps of the next round
+  uint64_t attempts;
+  uint64_t losers;
+  uint32_t max_active;
+  uint32_t pad;
+  uint32_t* Q;         // carried-loser queue, at least F*5/2+2 words
+};
+
 struct BatchLaunch {
   BatchHeader* hdr;
   BatchJob* jobs;
