@@ -241,6 +241,259 @@ def time_steps(torch, pip, A, seed, eps, steps, warmup, stream, opts):
     return [s.elapsed_time(e) for s, e in evs]
 
 
+def floor_ms(torch, pip, A, seed, stream, reps=3):
+    """Bare swap traffic of the same shuffle with no conflict resolution
+    (pip_calibrate_swap_floor): the practical floor of the round drivers."""
+    for _ in range(2):
+        pip.calibrate_swap_floor(A, seed=seed, stream=stream)
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        pip.calibrate_swap_floor(A, seed=seed, stream=stream)
+        e.record(stream)
+        e.synchronize()
+        out.append(s.elapsed_time(e))
+    return min(out)
+
+
+def run_batch(args):
+    """Batched workload: 8192 uint32 arrays A[i]=i, sizes log-uniform in
+    [2^8, 2^22] (stream seed 7), per-array seed = index, eps = 0.5.  One
+    launch (and its CUDA-graph replay) against one pip_shuffle per array."""
+    import numpy as np
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    import workloads
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    sizes, seeds = workloads.batch_workload(count=args.batch_count)
+    offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum((sizes + 3) // 4 * 4)  # 16-byte aligned arrays in one buffer
+    buf = torch.empty(int(offs[-1]), dtype=torch.int32, device="cuda")
+    arrays = [buf[int(offs[j]):int(offs[j]) + int(sizes[j])] for j in range(len(sizes))]
+    for a in arrays:
+        a.copy_(torch.arange(a.shape[0], dtype=torch.int32, device="cuda"))
+    total = int(sizes.sum())
+    eps = 0.5
+    b = pip.Batch(arrays, [int(x) for x in seeds], eps=eps)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.run()
+    pip.check()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s_, e_ in ev:
+            s_.record(stream)
+            b.run()
+            e_.record(stream)
+        pip.check()
+    batched_ms = [s_.elapsed_time(e_) for s_, e_ in ev]
+    # the same launch captured once and replayed
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        b.run(stream=side)
+    side.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        b.run(stream=side)
+    g.replay()
+    torch.cuda.synchronize()
+    gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gs.record()
+    for _ in range(args.steps):
+        g.replay()
+    ge.record()
+    torch.cuda.synchronize()
+    pip.check()
+    graph_ms = gs.elapsed_time(ge) / args.steps
+    # plain path: one launch per array, FIFO on one stream
+    plain_ms = []
+    for _ in range(max(1, args.plain_steps)):
+        ps, pe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ps.record()
+        for a, sd in zip(arrays, seeds):
+            pip.shuffle(a, seed=int(sd), eps=eps)
+        pe.record()
+        pip.check()
+        plain_ms.append(ps.elapsed_time(pe))
+    # identical output: the batch and the plain path applied the same number of
+    # shuffles to every array; compare both against a fresh re-run pair
+    chk = [j for j in range(0, len(sizes), max(1, len(sizes) // 64))]
+    ref = [torch.arange(int(sizes[j]), dtype=torch.int32, device="cuda") for j in chk]
+    bb = [torch.arange(int(sizes[j]), dtype=torch.int32, device="cuda") for j in chk]
+    pip.Batch(bb, [int(seeds[j]) for j in chk], eps=eps).run()
+    for r_, j in zip(ref, chk):
+        pip.shuffle(r_, seed=int(seeds[j]), eps=eps)
+    pip.check()
+    identical = all(bool(torch.equal(x, y)) for x, y in zip(ref, bb))
+    bms = sum(batched_ms) / len(batched_ms)
+    pms = sum(plain_ms) / len(plain_ms)
+    line = {
+        "metric": "shuffled elems/s (batched, 8192 arrays)",
+        "value": total / (bms / 1e3),
+        "unit": "elems/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": bms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"batch_{len(sizes)}_u32_log_uniform_2^8_2^22_seed7_eps0.5", "arrays": len(sizes),
+                   "total_elems": total, "fmax": b.plan.fmax, "block_threads": b.plan.block_threads,
+                   "l2": "inputs larger than L2 (no flush)"},
+        "graph_ms_per_step": graph_ms,
+        "graph_value": total / (graph_ms / 1e3),
+        "plain": {"ms_per_step": pms, "value": total / (pms / 1e3), "launches_per_step": len(sizes),
+                  "path": "pip_shuffle per array, FIFO on one stream"},
+        "speedup_vs_plain": pms / bms,
+        "identical_output_sample": identical,
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "step_ms": batched_ms,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def run_serve(args):
+    """Served workload: requests with sizes log-uniform in [2^12, 2^28]
+    (stream 5), uint32/uint64 by a seeded coin, seed = request id, eps = 0.5,
+    120 GB device budget.  Closed loop first (saturation throughput), then
+    Poisson arrivals at 80% of it; the same schedule through the plain
+    FIFO path (allocate, initialise, pip_shuffle, synchronize, one at a time)."""
+    import threading as th
+
+    import numpy as np
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    import workloads
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    N = args.requests
+    sizes, dtypes, seeds, _ = workloads.serve_workload(count=20000)
+    sizes, dtypes, seeds = sizes[:N], dtypes[:N], seeds[:N]
+    total = int(sizes.sum())
+    budget = 120 * 10**9
+    eps = 0.5
+    opts = dict(rounds_per_tick=args.rounds_per_tick, fresh_cap=args.fresh_cap)
+
+    def closed_loop():
+        with pip.Server(budget, **opts) as srv:
+            t0 = time.perf_counter()
+            tickets = [srv.submit(int(n), str(d), seed=int(s), eps=eps) for n, d, s in zip(sizes, dtypes, seeds)]
+            for t in tickets:
+                srv.wait(t)
+                srv.release(t)
+            dt = time.perf_counter() - t0
+            info = srv.info()
+        return dt, info
+
+    closed_loop()  # warm-up (kernel attributes, pools)
+    t_sat, info_sat = closed_loop()
+    rate = 0.8 * N / t_sat
+    _, _, _, arrivals = workloads.serve_workload(count=20000, rate_per_s=rate)
+    arrivals = arrivals[:N]
+
+    # open loop through the server
+    lat, done_at = [], []
+    with pip.Server(budget, **opts) as srv:
+        tickets = []
+        start = time.perf_counter()
+        start_ns = time.monotonic_ns()
+
+        def submitter():
+            for j in range(N):
+                delay = arrivals[j] - (time.perf_counter() - start)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(srv.submit(int(sizes[j]), str(dtypes[j]), seed=int(seeds[j]), eps=eps))
+
+        thr = th.Thread(target=submitter)
+        thr.start()
+        k = 0
+        while k < N:
+            if k >= len(tickets):
+                time.sleep(0.0005)
+                continue
+            _, st = srv.wait(tickets[k])
+            lat.append((st.done_ns - st.submit_ns) / 1e6)
+            done_at.append(st.done_ns)
+            srv.release(tickets[k])
+            k += 1
+        thr.join()
+        served_span = (max(done_at) - start_ns) / 1e9
+        info = srv.info()
+
+    # plain FIFO path, same arrivals
+    plain_lat = []
+    t0 = time.perf_counter()
+    for j in range(N):
+        delay = arrivals[j] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        n = int(sizes[j])
+        A = torch.arange(n, dtype=torch.int64 if dtypes[j] == "u64" else torch.int32, device="cuda")
+        pip.shuffle(A, seed=int(seeds[j]), eps=eps)
+        torch.cuda.synchronize()
+        plain_lat.append((time.perf_counter() - t0 - arrivals[j]) * 1e3)
+        del A
+    plain_span = time.perf_counter() - t0
+    # plain closed loop (back to back)
+    t1 = time.perf_counter()
+    for j in range(N):
+        n = int(sizes[j])
+        A = torch.arange(n, dtype=torch.int64 if dtypes[j] == "u64" else torch.int32, device="cuda")
+        pip.shuffle(A, seed=int(seeds[j]), eps=eps)
+        torch.cuda.synchronize()
+        del A
+    plain_sat = time.perf_counter() - t1
+    line = {
+        "metric": "served requests/s and p50/p99 latency vs FIFO plain path",
+        "value": N / served_span,
+        "unit": "requests/s",
+        "n_gpus": 1,
+        "steps": 1,
+        "warmup": 1,
+        "ms_per_step": served_span * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32/u64",
+        "data": "synthetic",
+        "config": {"workload": f"serve_{N}_of_20000_requests_log_uniform_2^12_2^28_eps0.5_budget120GB",
+                   "requests": N, "total_elems": total, "arrival_rate_per_s": rate, **opts},
+        "served": {"p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99), "throughput_req_s": N / served_span,
+                   "elems_s": total / served_span, "saturation_req_s": N / t_sat, "saturation_elems_s": total / t_sat,
+                   "peak_used_bytes": info.peak_used_bytes, "ticks": info.ticks},
+        "plain_fifo": {"p50_ms": _percentile(plain_lat, 50), "p99_ms": _percentile(plain_lat, 99),
+                       "throughput_req_s": N / plain_span, "elems_s": total / plain_span,
+                       "saturation_req_s": N / plain_sat, "saturation_elems_s": total / plain_sat},
+        "speedup_saturation": plain_sat / t_sat,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -261,10 +514,21 @@ def main():
     ap.add_argument("--grid-blocks", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--flags", type=int, default=0, help="PIP_FLAG_* bits (2 = L2 prefetch of the next block)")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=8192)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--rounds-per-tick", type=int, default=128)
+    ap.add_argument("--fresh-cap", type=int, default=1024)
+    ap.add_argument("--no-floor", action="store_true")
     args = ap.parse_args()
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
 
@@ -381,6 +645,13 @@ def main():
                           "aux_bytes": p_["aux_bytes"], "aux_bound_bytes": p_["aux_bound_bytes"],
                           "roofline_frac": ach / measured_peak_hbm()[0]}
 
+    # bare swap traffic of the same shuffle (scrambles A; nothing reads it after)
+    floor = None
+    if not args.no_floor:
+        f_ms = floor_ms(torch, pip, A, seed, stream)
+        floor = {"ms": f_ms, "elems_s": n / (f_ms / 1e3), "frac_of_floor": f_ms / ms_per_step,
+                 "what": "pip_calibrate_swap_floor: the n-1 swaps with no conflict resolution"}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -423,6 +694,7 @@ def main():
         "rounds": st.rounds,
         "loser_fraction": st.losers / max(1, st.attempts),
         "eps_sweep": sweep,
+        "random_swap_floor": floor,
         "step_ms": ms,
     }
     print(json.dumps(line), flush=True)

@@ -83,7 +83,8 @@ typedef struct {
 
 /* Tuning overrides; zero fields keep the planner's choice. */
 typedef struct {
-    double prefix_c;           /* C in F = C * n^(1-eps) (clamped so aux stays within the bound) */
+    double prefix_c;           /* C in F = C * n^(1-eps) (default 4 for one array, 1 for a batch;
+                                  clamped so aux stays within the bound) */
     uint32_t fresh_per_round;  /* explicit F (overrides prefix_c; still clamped by the bound) */
     uint32_t slot_factor;      /* reservation slots per active swap (2..16, default 4) */
     uint32_t grid_blocks;      /* persistent blocks (clamped to what can be co-resident) */
@@ -363,6 +364,17 @@ pip_status pip_check(void *stream);
  */
 pip_status pip_shuffle_noalloc(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed,
                                double eps, void *stream);
+
+/*
+ * pip_calibrate_swap_floor -- measurement probe, not a shuffle.  The paper has
+ * no counterpart; it is a tool for reading the round drivers' speed.
+ *   Performs the n-1 swaps A[i] <-> A[H[i]] (hashed targets of `seed`) all at
+ *   once with no conflict resolution, so A ends up with unspecified content
+ *   (its elements may be duplicated or lost).  Times taken around it give the
+ *   cost of the bare data movement of a shuffle on this GPU: coalesced i-side
+ *   accesses plus one random element read and write per swap.
+ */
+pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed, void *stream);
 
 /* pip_status_string -- static English description of a status code. */
 const char *pip_status_string(pip_status s);

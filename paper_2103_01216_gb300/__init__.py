@@ -229,6 +229,8 @@ def lib() -> ctypes.CDLL:
         L.pip_batch_run.restype = i32
         L.pip_shuffle_noalloc.argtypes = [vp, u64, i32, u64, dbl, vp]
         L.pip_shuffle_noalloc.restype = i32
+        L.pip_calibrate_swap_floor.argtypes = [vp, u64, i32, u64, vp]
+        L.pip_calibrate_swap_floor.restype = i32
         L.pip_serve_create.argtypes = [ctypes.POINTER(vp), u64, i32, ctypes.POINTER(ServeOptions)]
         L.pip_serve_create.restype = i32
         L.pip_serve_submit.argtypes = [vp, vp, u64, i32, u64, dbl, ctypes.POINTER(u64)]
@@ -509,3 +511,10 @@ class Server:
     def __exit__(self, *exc):
         self.close()
         return False
+
+
+def calibrate_swap_floor(A, seed: int = 0, stream=None) -> None:
+    """Measurement probe (``pip_calibrate_swap_floor``): the bare swap traffic of
+    a shuffle of ``A`` with no conflict resolution; leaves ``A`` unspecified."""
+    _raise(lib().pip_calibrate_swap_floor(A.data_ptr(), A.shape[0], tensor_dtype(A), seed, _stream_handle(stream)),
+           "pip_calibrate_swap_floor")

@@ -112,6 +112,10 @@ pip_status pip_batch_plan_make(const pip_batch_item* items, uint32_t count, pip_
   if (check_shape(0, dtype, eps) != PIP_OK) return PIP_EINVAL;
   pip_options o{};
   if (opt != nullptr) o = *opt;
+  // arrays of a batch share the device: C = 1 keeps each block's shared
+  // memory small enough for several resident arrays per SM
+  if (!(o.prefix_c > 0.0) && o.fresh_per_round == 0) o.prefix_c = 1.0;
+  opt = &o;
   const uint32_t sigma = o.slot_factor ? o.slot_factor : 4u;
   if (sigma < 2 || sigma > 16) return PIP_EINVAL;
   const uint32_t threads = o.block_threads ? o.block_threads : 256u;
@@ -145,6 +149,10 @@ pip_status pip_batch_prepare(const pip_batch_item* items, const pip_batch_plan* 
   if (plan == nullptr || jobs_dev == nullptr || (plan->count > 0 && items == nullptr)) return PIP_EINVAL;
   if (reinterpret_cast<uintptr_t>(jobs_dev) % 256 != 0) return PIP_EINVAL;
   const uint32_t fcap = cta_max_fmax(plan->slot_factor);
+  pip_options o{};
+  if (opt != nullptr) o = *opt;
+  if (!(o.prefix_c > 0.0) && o.fresh_per_round == 0) o.prefix_c = 1.0;  // as in pip_batch_plan_make
+  opt = &o;
   std::vector<char> host(plan->jobs_bytes, 0);
   BatchHeader* hdr = reinterpret_cast<BatchHeader*>(host.data());
   BatchJob* jobs = reinterpret_cast<BatchJob*>(host.data() + sizeof(BatchHeader));

@@ -19,7 +19,10 @@ namespace pip {
 namespace {
 
 constexpr uint64_t kAlign = 256;
-constexpr double kDefaultPrefixC = 1.0;
+// Default C in F = C * n^(1-eps) for a single array: large enough that the
+// scratch bound (or the L2 / shared-memory caps) decides, since fewer, larger
+// rounds are faster whenever the tables still fit.
+constexpr double kDefaultPrefixC = 4.0;
 constexpr uint32_t kDefaultSlotFactor = 4;
 constexpr uint32_t kDefaultThreads = 512;
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;

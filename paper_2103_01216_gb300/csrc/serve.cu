@@ -350,7 +350,7 @@ pip_status pip_serve_submit(pip_server* s, void* A_dev, uint64_t n, pip_dtype dt
   r->eps = eps;
   r->A = A_dev;
   pip_options o{};
-  o.prefix_c = s->opt.prefix_c;
+  o.prefix_c = s->opt.prefix_c > 0.0 ? s->opt.prefix_c : 1.0;
   r->F = n >= 2 ? cta_fresh(n, eps, &o, s->sigma, s->fmax) : 1u;
   r->array_bytes = n * eb;
   r->aux_bytes = req_aux_bytes(r->F);
