@@ -280,7 +280,12 @@ def run_batch(args):
         a.copy_(torch.arange(a.shape[0], dtype=torch.int32, device="cuda"))
     total = int(sizes.sum())
     eps = 0.5
-    b = pip.Batch(arrays, [int(x) for x in seeds], eps=eps)
+    bopts = {}
+    if args.block_threads:
+        bopts["block_threads"] = args.block_threads
+    if args.prefix_c:
+        bopts["prefix_c"] = args.prefix_c
+    b = pip.Batch(arrays, [int(x) for x in seeds], eps=eps, **bopts)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         b.run()
@@ -314,7 +319,7 @@ def run_batch(args):
     graph_ms = gs.elapsed_time(ge) / args.steps
     # plain path: one launch per array, FIFO on one stream
     plain_ms = []
-    for _ in range(max(1, args.plain_steps)):
+    for _ in range(args.plain_steps):
         ps, pe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ps.record()
         for a, sd in zip(arrays, seeds):
@@ -333,7 +338,7 @@ def run_batch(args):
     pip.check()
     identical = all(bool(torch.equal(x, y)) for x, y in zip(ref, bb))
     bms = sum(batched_ms) / len(batched_ms)
-    pms = sum(plain_ms) / len(plain_ms)
+    pms = sum(plain_ms) / len(plain_ms) if plain_ms else float("nan")
     line = {
         "metric": "shuffled elems/s (batched, 8192 arrays)",
         "value": total / (bms / 1e3),

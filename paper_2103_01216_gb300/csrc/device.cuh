@@ -139,35 +139,42 @@ __device__ __forceinline__ void set_status(uint32_t* status, uint32_t code) {
 // The wait gives up after `timeout_ns`, or as soon as another block has
 // recorded an error, and the function then returns false (status set) so the
 // caller can leave the kernel; every block then exits at its next barrier.
+// One thread's part of the barrier: arrive (release) unless `arrive` is
+// false, then wait (acquire) for barrier number `epoch` to complete, bounded
+// by `timeout_ns` and by an error recorded elsewhere.  Returns 1 on success.
+__device__ __forceinline__ uint32_t barrier_arrive_wait(unsigned long long* counter, uint32_t nblocks,
+                                                        uint64_t epoch, uint32_t* status, uint64_t timeout_ns,
+                                                        bool arrive) {
+  uint32_t ok = 1;
+  const uint64_t target = (epoch + 1) * (uint64_t)nblocks;
+  if (arrive) {
+    __threadfence();
+    red_release_add_u64(counter, 1ull);
+  }
+  uint64_t t0 = 0;
+  uint32_t polls = 0;
+  while (ld_acquire_u64(counter) < target) {
+    if ((++polls & 63u) == 0) {
+      if (ld_relaxed_u32(status) != 0u) { ok = 0; break; }
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > timeout_ns) {
+        set_status(status, PIP_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  if (ok && ld_relaxed_u32(status) != 0u) ok = 0;
+  return ok;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned long long* counter, uint32_t nblocks,
                                              uint64_t& epoch, uint32_t* status,
                                              uint64_t timeout_ns, bool arrive = true) {
   __shared__ uint32_t s_ok;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t ok = 1;
-    const uint64_t target = (epoch + 1) * (uint64_t)nblocks;
-    if (arrive) {
-      __threadfence();
-      red_release_add_u64(counter, 1ull);
-    }
-    uint64_t t0 = 0;
-    uint32_t polls = 0;
-    while (ld_acquire_u64(counter) < target) {
-      if ((++polls & 63u) == 0) {
-        if (ld_relaxed_u32(status) != 0u) { ok = 0; break; }
-        const uint64_t now = globaltimer_ns();
-        if (t0 == 0) t0 = now;
-        else if (now - t0 > timeout_ns) {
-          set_status(status, PIP_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    if (ok && ld_relaxed_u32(status) != 0u) ok = 0;
-    s_ok = ok;
-  }
+  if (threadIdx.x == 0) s_ok = barrier_arrive_wait(counter, nblocks, epoch, status, timeout_ns, arrive);
   __syncthreads();
   epoch += 1;
   return s_ok != 0u;

@@ -118,7 +118,7 @@ pip_status pip_batch_plan_make(const pip_batch_item* items, uint32_t count, pip_
   opt = &o;
   const uint32_t sigma = o.slot_factor ? o.slot_factor : 4u;
   if (sigma < 2 || sigma > 16) return PIP_EINVAL;
-  const uint32_t threads = o.block_threads ? o.block_threads : 256u;
+  const uint32_t threads = o.block_threads ? o.block_threads : 1024u;  // measured best for the 8192-array mix
   if (threads < 128 || threads > 1024 || threads % 32 != 0) return PIP_EINVAL;
   const uint32_t eb = elem_bytes_of(dtype);
   const uint32_t fcap = cta_max_fmax(sigma);
