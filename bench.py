@@ -369,6 +369,25 @@ def run_batch(args):
     return 0
 
 
+def run_floor(args):
+    """The bare swap traffic of the workload (pip_calibrate_swap_floor): the
+    n-1 swaps with no conflict resolution, timed like a shuffle step."""
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    A = make_device_input(torch, args.n, args.dtype, "cuda")
+    stream = torch.cuda.current_stream()
+    f = floor_ms(torch, pip, A, args.seed, stream, reps=max(1, args.steps))
+    print(json.dumps({"metric": "bare swap floor", "value": args.n / (f / 1e3), "unit": "swaps/s", "ms": f,
+                      "n": args.n, "dtype": args.dtype, "bytes_algorithmic_per_swap": BYTES_PER_ELEM[args.dtype]}),
+          flush=True)
+    return 0
+
+
 def _percentile(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -519,7 +538,7 @@ def main():
     ap.add_argument("--grid-blocks", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--flags", type=int, default=0, help="PIP_FLAG_* bits (2 = L2 prefetch of the next block)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "floor"])
     ap.add_argument("--batch-count", type=int, default=8192)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--requests", type=int, default=1000)
@@ -534,6 +553,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "floor":
+        return run_floor(args)
 
     import torch
 

@@ -436,10 +436,6 @@ pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint
   const uint32_t maxb = grid_driver_max_blocks(plan.elem_bytes, H != nullptr, plan.threads);
   if (maxb == 0) return PIP_ECUDA;
   blocks = std::max(1u, std::min(blocks, maxb));
-  if (const char* e = std::getenv("PIP_L2_FETCH_BYTES")) {
-    cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)std::atoi(e));
-    cudaGetLastError();
-  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(plan.threads);
