@@ -312,7 +312,8 @@ def shuffle_ptr(ptr: int, n: int, dtype: int, seed: int, eps: float, *, H_ptr: i
     _raise(rc, "pip_shuffle_ex")
 
 
-def shuffle(A, seed: int = 0, eps: float = 0.5, *, H=None, stream=None, aux=None, stats=None, **options) -> None:
+def shuffle(A, seed: int = 0, eps: float = 0.5, *, H=None, stream=None, aux=None, stats=None, tuned: bool = False,
+            **options) -> None:
     """Knuth-shuffle the CUDA tensor ``A`` in place (asynchronous on ``stream``).
 
     ``H``: optional CUDA uint32/int32 tensor of explicit targets (0 <= H[i] <= i).
@@ -324,6 +325,10 @@ def shuffle(A, seed: int = 0, eps: float = 0.5, *, H=None, stream=None, aux=None
         raise ValueError("A must be a contiguous CUDA tensor")
     d = tensor_dtype(A)
     n = A.shape[0]
+    if tuned:  # options cached by the autotuner for this size class (explicit options win)
+        from . import autotune
+
+        options = {**autotune.options_for(n, {U32: "u32", U64: "u64", REC128: "rec128"}[d], eps), **options}
     h_ptr = None
     if H is not None:
         if not H.is_cuda or H.element_size() != 4 or H.dim() != 1 or H.shape[0] != n or not H.is_contiguous():

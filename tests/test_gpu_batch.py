@@ -133,3 +133,21 @@ def test_batch_workload_sample(pip):
     pip.check()
     for a, d, j in zip(host, dev, idx):
         assert np.array_equal(from_dev(d, a), expected(a, int(seeds[j])))
+
+
+def test_autotuned_options_keep_the_output(pip, tmp_path, monkeypatch):
+    from paper_2103_01216_gb300 import autotune
+
+    monkeypatch.setenv("PIP_TUNE_CACHE", str(tmp_path / "tune.json"))
+    n = (1 << 16) + 3
+    entry = autotune.tune_single(n, "u64", 0.5, reps=1)
+    assert entry["options"] and entry["ms"] > 0
+    host = workloads.iota(n, "u64")
+    A = to_dev(host)
+    pip.shuffle(A, seed=5, eps=0.5, tuned=True)
+    pip.check()
+    assert np.array_equal(from_dev(A, host), expected(host, 5))
+    sizes = [300, 5000, 70000]
+    arrays = [to_dev(workloads.iota(s, "u32")) for s in sizes]
+    b = autotune.tune_batch(arrays, [1, 2, 3], eps=0.5, reps=1)
+    assert b["options"]
