@@ -146,6 +146,23 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """Maximum of a per-rank time over all ranks (identity without a process
+    group).  Replicas run independently; only the timing is combined."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job elements/s: every rank shuffled n_per_rank elements per step."""
+    return world * n_per_rank * steps / (max_ms / 1e3)
+
+
 def cpu_oracle_sample(dtype: str, seed: int, n_sample: int):
     """Times the oracle (single thread) on n_sample elements; returns elems/s and seconds."""
     import numpy as np
@@ -605,13 +622,9 @@ def main():
         ms = time_steps(torch, pip, A, seed, eps, args.steps, args.warmup, stream, opts)
         torch.cuda.synchronize()
     clocks = clk.summary()
-    total_ms = sum(ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), dist, device)
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms / 1e3)
+    value = replica_throughput(n, world, args.steps, total_ms)
 
     # aux bytes as seen by the allocator while a shuffle is in flight
     side = torch.cuda.Stream()
@@ -649,12 +662,8 @@ def main():
             out.copy_(dev, non_blocking=True)
         e.record()
         pip.check()
-        e2e_ms = s.elapsed_time(e)
-        if dist is not None:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * n * args.e2e_steps / (e2e_ms / 1e3), "unit": "elems/s",
+        e2e_ms = max_over_ranks(s.elapsed_time(e), dist, device)
+        e2e = {"value": replica_throughput(n, world, args.e2e_steps, e2e_ms), "unit": "elems/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "ms_per_step": e2e_ms / args.e2e_steps}
         del host, out, dev
@@ -714,8 +723,8 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
-        "plan": {k: plan[k] for k in ("fresh_per_round", "max_active", "slots", "grid_blocks", "block_threads",
-                                      "aux_bytes", "aux_bound_bytes", "min_rounds")},
+        "plan": {k: plan[k] for k in ("driver", "fresh_per_round", "max_active", "slots", "grid_blocks",
+                                      "block_threads", "aux_bytes", "smem_bytes", "aux_bound_bytes", "min_rounds")},
         "aux_alloc_delta_bytes": aux_delta,
         "rounds": st.rounds,
         "loser_fraction": st.losers / max(1, st.attempts),
