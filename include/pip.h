@@ -73,7 +73,7 @@ typedef struct {
     uint64_t aux_bytes;        /* exact device scratch bytes this plan allocates */
     uint64_t aux_bound_bytes;  /* c*n^(1-eps) + 4096 with c = PIP_AUX_C: the bound aux_bytes obeys */
     uint64_t min_rounds;       /* ceil((n-1)/F): a lower bound on the rounds */
-    uint32_t driver;           /* 0 = persistent grid, 1 = one block with shared-memory tables */
+    uint32_t driver;           /* 0 = persistent grid, 1 = one block, 2 = one cluster (shared-memory tables) */
     uint32_t pad;
     uint64_t smem_bytes;       /* on-chip scratch of the one-block driver (counted in the bound) */
 } pip_plan_info;
@@ -110,6 +110,9 @@ typedef struct {
  * memory run on one block, larger prefixes on the persistent grid. */
 #define PIP_FLAG_FORCE_GRID 32u
 #define PIP_FLAG_FORCE_CTA 64u
+/* One thread-block cluster (up to 16 CTAs) with the tables in distributed
+ * shared memory: the default for prefixes too large for one block. */
+#define PIP_FLAG_FORCE_CLUSTER 128u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {

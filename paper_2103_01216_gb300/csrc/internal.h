@@ -19,7 +19,7 @@ struct Ctrl {
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is one 256-byte line pair");
 
-enum Driver : uint32_t { kDriverGrid = 0, kDriverCta = 1 };
+enum Driver : uint32_t { kDriverGrid = 0, kDriverCta = 1, kDriverCluster = 2 };
 
 struct Plan {
   uint32_t driver = kDriverGrid;
@@ -131,6 +131,14 @@ pip_status launch_cta_driver(const BatchLaunch& bl, cudaStream_t stream);
 // the kernel, on `stream`; `aux` holds the 256-byte Ctrl block.
 pip_status launch_cta_single(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
                              pip_stats* stats, cudaStream_t stream);
+
+// Cluster driver (cluster_driver.cu): shared memory per CTA for a cluster of
+// `cs` CTAs and fresh block F; whether such a launch fits on this device;
+// the launch itself (plan.blocks = cluster size).
+uint64_t cluster_cta_smem(uint32_t F, uint32_t sigma, uint32_t cs);
+bool cluster_supported(uint32_t elem_bytes, uint32_t cs, uint32_t threads, uint64_t smem);
+pip_status launch_cluster_driver(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
+                                 pip_stats* stats, cudaStream_t stream);
 
 // Device facts cached per device.
 struct DeviceInfo {

@@ -112,8 +112,17 @@ uint32_t cta_fresh(uint64_t n, double eps, const pip_options* opt, uint32_t sigm
   else want = (o.prefix_c > 0.0 ? o.prefix_c : kDefaultPrefixC) * x;
   uint64_t F = (uint64_t)std::max(1.0, std::ceil(want));
   F = std::min<uint64_t>({F, n - 1, (uint64_t)std::max(1u, fcap)});
-  // device bytes (the 256-byte control block) plus shared memory stay in the bound
-  while (F > 1 && sizeof(Ctrl) + cta_job_bytes((uint32_t)F, sigma) > bound) --F;
+  // device bytes (the 256-byte control block) plus shared memory stay in the
+  // bound: largest such F by bisection (the cost grows with F)
+  if (sizeof(Ctrl) + cta_job_bytes((uint32_t)F, sigma) > bound) {
+    uint64_t lo = 1, hi = F;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi + 1) / 2;
+      if (sizeof(Ctrl) + cta_job_bytes((uint32_t)mid, sigma) <= bound) lo = mid;
+      else hi = mid - 1;
+    }
+    F = lo;
+  }
   return (uint32_t)F;
 }
 
@@ -165,10 +174,72 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
   if (p.aux_bytes > p.aux_bound) return PIP_EINVAL;  // cannot happen for n >= 2: F=1 needs ~2.3 KB
 
   p.sigma = slot_factor;
-  // one block with shared-memory tables when the prefix fits there (forced
-  // either way by the flags)
+  // Driver choice.  Each driver has its own scratch cost per fresh swap; the
+  // cheapest one whose own memory cap does not cut the (bound-limited)
+  // prefix wins: one block, then one cluster, then the persistent grid.
+  // The flags force a driver.
   const uint32_t fcap = cta_max_fmax(slot_factor);
-  const bool want_cta = (o.flags & PIP_FLAG_FORCE_CTA) || (!(o.flags & PIP_FLAG_FORCE_GRID) && F <= fcap);
+  const uint64_t F_req = std::min<uint64_t>(
+      n - 1, (uint64_t)std::max(1.0, std::ceil(o.fresh_per_round ? (double)o.fresh_per_round
+                                                                   : (o.prefix_c > 0.0 ? o.prefix_c : kDefaultPrefixC) * x)));
+  // Measured on GB300 (prefix sweep over the three drivers, n = 2^26): one
+  // block costs 2.3-2.6 us per round up to F ~ 512 and degrades beyond ~1K
+  // (one SM); a 16-CTA cluster costs 3.1-4.0 us per round for F in 1K-4K;
+  // the grid costs 4.5-5 us per round at small F and wins from F ~ 6-8K on
+  // (its throughput scales with the whole GPU).
+  constexpr uint32_t kCtaMaxF = 768, kGridMinF = 6000;
+  const uint32_t F_cta_nocap = cta_fresh(n, eps, opt, slot_factor, 0xFFFFFFFFu);
+  const bool forced = (o.flags & (PIP_FLAG_FORCE_GRID | PIP_FLAG_FORCE_CTA | PIP_FLAG_FORCE_CLUSTER)) != 0;
+  bool want_cta = (o.flags & PIP_FLAG_FORCE_CTA) || (!forced && F_cta_nocap <= std::min(fcap, kCtaMaxF));
+  const bool grid_large = F >= kGridMinF;  // F here is the grid plan's (bound- and L2-limited) prefix
+  // cluster: 16 CTAs when the device allows that many, else 8
+  const uint32_t cl_threads = o.block_threads ? threads : 256u;
+  uint32_t cl_cs = 0, F_cl = 0;
+  if (!want_cta && !(o.flags & PIP_FLAG_FORCE_GRID) && have_dev &&
+      ((o.flags & PIP_FLAG_FORCE_CLUSTER) || !grid_large)) {
+    for (uint32_t cs : {16u, 8u}) {
+      // largest F within the bound: shared memory of all CTAs + control block + two loser queues
+      uint64_t lo = 1, hi = F_req;
+      auto cost = [&](uint64_t f) {
+        const uint64_t km = f * 5 / 2 + 2;
+        return cluster_cta_smem((uint32_t)f, slot_factor, cs) * cs + sizeof(Ctrl) + 2 * align_up(4 * km);
+      };
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) / 2;
+        if (cost(mid) <= p.aux_bound) lo = mid;
+        else hi = mid - 1;
+      }
+      const uint64_t F_b = lo;
+      if (cluster_supported(eb, cs, cl_threads, cluster_cta_smem((uint32_t)F_b, slot_factor, cs))) {
+        cl_cs = cs;
+        F_cl = (uint32_t)F_b;
+        break;
+      }
+    }
+  }
+  const bool want_cluster =
+      cl_cs != 0 && ((o.flags & PIP_FLAG_FORCE_CLUSTER) || (!forced && !want_cta && !grid_large));
+  if (o.flags & PIP_FLAG_FORCE_CLUSTER && cl_cs == 0) return PIP_EINVAL;
+  if (want_cluster) {
+    p.driver = kDriverCluster;
+    p.F = F_cl;
+    p.kmax = p.F * 5 / 2 + 2;
+    p.nslots = slot_factor * p.F + 32;
+    p.blocks = cl_cs;
+    p.threads = cl_threads;
+    p.smem_bytes = cluster_cta_smem(p.F, slot_factor, cl_cs) * cl_cs;
+    p.off_Q[0] = align_up(sizeof(Ctrl));
+    p.off_Q[1] = p.off_Q[0] + align_up(4ull * p.kmax);
+    p.aux_bytes = p.off_Q[1] + align_up(4ull * p.kmax);
+    p.timeout_ns = o.wait_timeout_ns ? o.wait_timeout_ns : kDefaultTimeoutNs;
+    p.deadline_ns = 60000000000ull + 5000ull * (p.n / p.F + 1) + 20ull * p.n;
+    if (const char* e = std::getenv("PIP_DEADLINE_MS")) {
+      const long long ms = std::atoll(e);
+      if (ms > 0) p.deadline_ns = (uint64_t)ms * 1000000ull;
+    }
+    *out = p;
+    return PIP_OK;
+  }
   if (want_cta) {
     p.driver = kDriverCta;
     p.F = cta_fresh(n, eps, opt, slot_factor, fcap);

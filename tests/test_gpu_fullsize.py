@@ -135,7 +135,8 @@ def test_scratch_is_exactly_the_plan(pip, eps):
     A = torch.arange(n, dtype=torch.int64, device="cuda")
     aux = torch.empty(p["aux_bytes"], dtype=torch.uint8, device="cuda")
     small = torch.arange(1 << 16, dtype=torch.int64, device="cuda")
-    pip.shuffle(small, seed=4, eps=eps, aux=aux, flags=32 if p["driver"] == pip.DRIVER_GRID else 64)  # loads the kernel
+    flag = {pip.DRIVER_GRID: 32, pip.DRIVER_CTA: 64, pip.DRIVER_CLUSTER: 128}[p["driver"]]
+    pip.shuffle(small, seed=4, eps=eps, aux=aux, flags=flag)  # loads the kernel
     pip.check()
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()

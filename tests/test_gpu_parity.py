@@ -24,8 +24,8 @@ def pip():
     return load_pip()
 
 
-# both round drivers: the persistent grid and the one-block shared-memory driver
-DRIVERS = {"grid": 32, "cta": 64}
+# the three round drivers: persistent grid, one block, one cluster (DSMEM tables)
+DRIVERS = {"grid": 32, "cta": 64, "cluster": 128}
 
 
 def expect_hashed(arr, seed):
@@ -181,6 +181,9 @@ def test_output_does_not_depend_on_launch_shape(pip):
         dict(flags=DRIVERS["cta"], fresh_per_round=17, slot_factor=2),
         dict(flags=DRIVERS["cta"], fresh_per_round=3000, slot_factor=8, block_threads=256),
         dict(flags=DRIVERS["grid"], fresh_per_round=3000),
+        dict(flags=DRIVERS["cluster"]),
+        dict(flags=DRIVERS["cluster"], fresh_per_round=50000, slot_factor=3),
+        dict(flags=DRIVERS["cluster"], fresh_per_round=7, block_threads=256),
     ]
     for c in configs:
         out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5, **c)
