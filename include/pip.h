@@ -113,6 +113,10 @@ typedef struct {
 /* One thread-block cluster (up to 16 CTAs) with the tables in distributed
  * shared memory: the default for prefixes too large for one block. */
 #define PIP_FLAG_FORCE_CLUSTER 128u
+/* Grid driver: issue a swap's array loads together with its reservation
+ * checks instead of after them (one memory round trip less per round, extra
+ * loads for the swaps that lose).  Performance only; results are identical. */
+#define PIP_FLAG_SPECULATE 256u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {

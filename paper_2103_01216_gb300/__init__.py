@@ -183,6 +183,7 @@ FLAG_ARRAY_STORE_EVICT_FIRST = 16
 FLAG_FORCE_GRID = 32
 FLAG_FORCE_CTA = 64
 FLAG_FORCE_CLUSTER = 128
+FLAG_SPECULATE = 256
 
 _lock = threading.Lock()
 _lib = None

@@ -46,6 +46,7 @@ struct ClusterArgs {
   pip_stats* stats;
   uint32_t* latch;
   uint64_t deadline_ns;
+  uint32_t prefetch;
 };
 
 template <bool kExplicit>
@@ -174,10 +175,17 @@ __global__ void __launch_bounds__(1024) cluster_rounds_kernel(const ClusterArgs 
         }
       }
     }
-    // ---- fresh block W_{r+1} reserves
+    // ---- fresh block W_{r+1} reserves (optionally pulling the array lines it
+    // will swap into L2 one round ahead)
     for (uint32_t i = Ln + g; i < L; i += T) {
       const uint32_t h = cl_target<kExplicit>(a, i);
-      if (h != i) reserve(nb, Ln, L, h, i + 1u);
+      if (h != i) {
+        reserve(nb, Ln, L, h, i + 1u);
+        if (a.prefetch) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A + h));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i));
+        }
+      }
     }
     cl.sync();
     const uint32_t nl_next = cnt0[nb];
@@ -323,6 +331,7 @@ pip_status launch_cluster_driver(const Plan& plan, void* A, const uint32_t* H, u
   a.stats = stats;
   a.latch = error_latch_ptr();
   a.deadline_ns = plan.deadline_ns;
+  a.prefetch = (plan.flags & PIP_FLAG_PREFETCH) ? 1u : 0u;
   if (a.latch == nullptr) return PIP_ECUDA;
   if (cudaMemsetAsync(aux, 0, sizeof(Ctrl), stream) != cudaSuccess) return PIP_ECUDA;
   if (H != nullptr) {

@@ -44,7 +44,8 @@ __device__ __forceinline__ void sclear(uint32_t* p, uint32_t count) {
 // *rs.  Returns the status (0 = ok).  All control decisions are block-uniform.
 template <typename Elem>
 __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, uint32_t sigma, uint64_t deadline_ns,
-                            uint64_t t_start, pip_job_stats* st, ResumeState* rs, uint32_t budget) {
+                            uint64_t t_start, pip_job_stats* st, ResumeState* rs, uint32_t budget,
+                            bool prefetch = false) {
   __shared__ uint32_t s_cnt[2];
   __shared__ uint32_t s_abort;
   const uint32_t n = job.n;
@@ -180,10 +181,17 @@ __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, 
           }
         }
       }
-      // ---- fresh block W_{r+1} reserves
+      // ---- fresh block W_{r+1} reserves (and, for a lone array, pulls the
+      // array lines it will swap into L2 one round ahead)
       for (uint32_t i = Ln + tid; i < L; i += NT) {
         const uint32_t h = job_target(job, i);
-        if (h != i) sreserve(Dnb, Snb, ns, Ln, L, h, i + 1u);
+        if (h != i) {
+          sreserve(Dnb, Snb, ns, Ln, L, h, i + 1u);
+          if (prefetch) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + h));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + i));
+          }
+        }
       }
       __syncthreads();
       const uint32_t nl_next = s_cnt[nb];

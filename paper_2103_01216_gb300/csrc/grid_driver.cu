@@ -206,6 +206,17 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
           hh[j] = act[j] ? target_of<kExplicit>(a, ii[j]) : 0u;
           act[j] = act[j] && hh[j] != ii[j];  // self-loops finish at once
         }
+        Elem x[kU], y[kU];
+        const bool spec = (a.flags & PIP_FLAG_SPECULATE) != 0u;
+        if (spec) {  // array loads issued before the decision (wasted for losers)
+#pragma unroll
+          for (int j = 0; j < kU; ++j) {
+            if (act[j]) {
+              x[j] = ld_hint(A + ii[j], pol.arr);
+              y[j] = ld_hint(A + hh[j], pol.arr);
+            }
+          }
+        }
 #pragma unroll
         for (int j = 0; j < kU; ++j) {
           own[j] = 0;
@@ -218,7 +229,6 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
           }
         }
         bool win[kU];
-        Elem x[kU], y[kU];
 #pragma unroll
         for (int j = 0; j < kU; ++j) {
           const uint32_t i = ii[j];
@@ -226,7 +236,7 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
           // the slot of i has a priority at most i+1 (so none targets i)
           const bool own_free = (i < Lprev) ? (own[j] == 0u) : (own[j] <= i + 1u);
           win[j] = act[j] && own_free && rh[j] == i + 1u;
-          if (win[j]) {
+          if (win[j] && !spec) {
             x[j] = ld_hint(A + ii[j], pol.arr);
             y[j] = ld_hint(A + hh[j], pol.arr);
           }

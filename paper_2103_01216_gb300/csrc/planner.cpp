@@ -248,7 +248,10 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
     p.smem_bytes = cta_job_bytes(p.F, slot_factor);
     p.aux_bytes = sizeof(Ctrl);
     p.blocks = 1;
-    p.threads = o.block_threads ? threads : 1024;
+    // measured on the eps = 0.75 workload: 512 threads and the one-round-ahead
+    // L2 prefetch of the array lines cut a round from 2.46 to 1.97 us
+    p.threads = o.block_threads ? threads : 512;
+    p.flags |= PIP_FLAG_PREFETCH;
     uint64_t tmo = o.wait_timeout_ns ? o.wait_timeout_ns : kDefaultTimeoutNs;
     p.timeout_ns = tmo;
     p.deadline_ns = 60000000000ull + 5000ull * (p.n / p.F + 1) + 20ull * p.n;
@@ -275,6 +278,9 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
     if (ms > 0 && !o.wait_timeout_ns) tmo = (uint64_t)ms * 1000000ull;
   }
   p.timeout_ns = tmo;
+  // small prefixes are latency-bound: issue the array loads with the checks
+  // (measured 2-7 % faster up to F ~ 50K, 27 % slower at F ~ 1.1M)
+  if (p.F <= 131072u) p.flags |= PIP_FLAG_SPECULATE;
   // whole-run limit: far above any legitimate run (about 1 us per round plus
   // 1 ns per element would already be slow), so only a defect can reach it
   uint64_t deadline = 60000000000ull + 2000ull * (p.n / p.F + 1) + 20ull * p.n;

@@ -184,6 +184,8 @@ def test_output_does_not_depend_on_launch_shape(pip):
         dict(flags=DRIVERS["cluster"]),
         dict(flags=DRIVERS["cluster"], fresh_per_round=50000, slot_factor=3),
         dict(flags=DRIVERS["cluster"], fresh_per_round=7, block_threads=256),
+        dict(flags=DRIVERS["grid"] | 256, fresh_per_round=3000),
+        dict(flags=DRIVERS["grid"] | 256, fresh_per_round=50000),
     ]
     for c in configs:
         out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5, **c)
