@@ -436,15 +436,15 @@ def run_serve(args):
     total = int(sizes.sum())
     budget = 120 * 10**9
     eps = 0.5
-    opts = dict(rounds_per_tick=args.rounds_per_tick, fresh_cap=args.fresh_cap)
+    opts = dict(rounds_per_tick=args.rounds_per_tick, fresh_cap=args.fresh_cap, tick_us=args.tick_us)
 
     def closed_loop():
         with pip.Server(budget, **opts) as srv:
             t0 = time.perf_counter()
-            tickets = [srv.submit(int(n), str(d), seed=int(s), eps=eps) for n, d, s in zip(sizes, dtypes, seeds)]
-            for t in tickets:
-                srv.wait(t)
-                srv.release(t)
+            for n, d, s in zip(sizes, dtypes, seeds):
+                srv.submit(int(n), str(d), seed=int(s), eps=eps)
+            for _ in range(N):  # release each request as soon as it finishes
+                srv.release(srv.next_done())
             dt = time.perf_counter() - t0
             info = srv.info()
         return dt, info
@@ -471,20 +471,21 @@ def run_serve(args):
 
         thr = th.Thread(target=submitter)
         thr.start()
-        k = 0
-        while k < N:
-            if k >= len(tickets):
-                time.sleep(0.0005)
-                continue
-            _, st = srv.wait(tickets[k])
+        for _ in range(N):  # completion order: each request is released as soon as it is done
+            t = srv.next_done()
+            _, st = srv.poll(t)
             lat.append((st.done_ns - st.submit_ns) / 1e6)
             done_at.append(st.done_ns)
-            srv.release(tickets[k])
-            k += 1
+            srv.release(t)
         thr.join()
         served_span = (max(done_at) - start_ns) / 1e9
         info = srv.info()
 
+    if args.no_plain:
+        print(json.dumps({"served_saturation_req_s": N / t_sat, "saturation_elems_s": total / t_sat,
+                          "p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99),
+                          "throughput_req_s": N / served_span, "ticks": info.ticks, **opts}), flush=True)
+        return 0
     # plain FIFO path, same arrivals
     plain_lat = []
     t0 = time.perf_counter()
@@ -559,9 +560,11 @@ def main():
     ap.add_argument("--batch-count", type=int, default=8192)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--requests", type=int, default=1000)
-    ap.add_argument("--rounds-per-tick", type=int, default=128)
+    ap.add_argument("--rounds-per-tick", type=int, default=0)
+    ap.add_argument("--tick-us", type=int, default=0)
     ap.add_argument("--fresh-cap", type=int, default=1024)
     ap.add_argument("--no-floor", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="serve: skip the plain FIFO comparison")
     args = ap.parse_args()
 
     if args.impl == "reference":

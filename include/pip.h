@@ -242,12 +242,12 @@ typedef struct pip_server pip_server;
 
 /* Server tuning; zero fields keep the defaults. */
 typedef struct {
-    uint32_t max_resident;     /* requests on the device at once (default 1024) */
-    uint32_t rounds_per_tick;  /* rounds each resident request advances per tick (default 128) */
+    uint32_t max_resident;     /* requests on the device at once (default: one per tick block) */
+    uint32_t rounds_per_tick;  /* cap on the rounds a request advances per tick (default: no cap) */
     uint32_t fresh_cap;        /* cap on a request's fresh block F (default 1024; one block each) */
     uint32_t slot_factor;      /* reservation slots per fresh swap (default 4) */
     uint32_t block_threads;    /* threads per block of the tick kernel (default 512) */
-    uint32_t pad;
+    uint32_t tick_us;          /* GPU time budget of one tick, shared by the resident requests (default 1000) */
     double prefix_c;           /* C in F = C * n^(1-eps) (default 1) */
 } pip_serve_options;
 
@@ -288,9 +288,9 @@ typedef struct {
  * A background thread repeats ticks: it admits waiting requests in arrival
  * order while budget_bytes allows, charging each request its array
  * (n * element bytes) plus its O(n^(1-eps)) scratch; it then advances every
- * resident request by up to rounds_per_tick rounds in one launch (each
- * request on one block, round state kept in device memory between ticks),
- * and retires finished ones.  Requests arriving meanwhile join at the next
+ * resident request, most remaining work first, for a slice of the tick's
+ * time budget in one launch (each request on one block, round state kept in
+ * device memory between ticks), and retires finished ones.  Requests arriving meanwhile join at the next
  * tick, so their work overlaps on the device with the requests already
  * running (continuous batching).  The result of every request equals
  * pip_shuffle on the same array, seed and eps.
@@ -317,6 +317,12 @@ pip_status pip_serve_poll(pip_server *srv, uint64_t ticket, void **A_out, pip_re
 /* pip_serve_wait -- pip_serve_poll that blocks up to timeout_ms. */
 pip_status pip_serve_wait(pip_server *srv, uint64_t ticket, uint32_t timeout_ms, void **A_out,
                           pip_req_stats *st);
+
+/* pip_serve_next_done -- the ticket of a finished request not yet returned by
+ * this call, in completion order; blocks up to timeout_ms (PIP_EAGAIN when
+ * none finished in time).  Lets a client release each request as soon as it
+ * is done, whatever the submission order. */
+pip_status pip_serve_next_done(pip_server *srv, uint32_t timeout_ms, uint64_t *ticket);
 
 /* pip_serve_release -- forgets a finished request, frees its array if the
  * server allocated it, and returns its charge to the budget. PIP_EAGAIN if

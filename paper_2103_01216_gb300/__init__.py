@@ -135,7 +135,7 @@ class ServeOptions(ctypes.Structure):
         ("fresh_cap", ctypes.c_uint32),
         ("slot_factor", ctypes.c_uint32),
         ("block_threads", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("tick_us", ctypes.c_uint32),
         ("prefix_c", ctypes.c_double),
     ]
 
@@ -241,6 +241,8 @@ def lib() -> ctypes.CDLL:
         L.pip_serve_poll.restype = i32
         L.pip_serve_wait.argtypes = [vp, u64, u32, ctypes.POINTER(vp), ctypes.POINTER(ReqStats)]
         L.pip_serve_wait.restype = i32
+        L.pip_serve_next_done.argtypes = [vp, u32, ctypes.POINTER(u64)]
+        L.pip_serve_next_done.restype = i32
         L.pip_serve_release.argtypes = [vp, u64]
         L.pip_serve_release.restype = i32
         L.pip_serve_info_get.argtypes = [vp, ctypes.POINTER(ServeInfo)]
@@ -497,6 +499,15 @@ class Server:
         rc = lib().pip_serve_wait(self._h, ticket, timeout_ms, ctypes.byref(p), ctypes.byref(st))
         _raise(rc, "pip_serve_wait")
         return p.value or 0, st
+
+    def next_done(self, timeout_ms: int = 600000):
+        """Ticket of the next finished request (completion order), or None on timeout."""
+        t = ctypes.c_uint64()
+        rc = lib().pip_serve_next_done(self._h, timeout_ms, ctypes.byref(t))
+        if rc == PIP_EAGAIN:
+            return None
+        _raise(rc, "pip_serve_next_done")
+        return t.value
 
     def release(self, ticket: int) -> None:
         _raise(lib().pip_serve_release(self._h, ticket), "pip_serve_release")

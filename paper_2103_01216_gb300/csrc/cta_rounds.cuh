@@ -45,9 +45,11 @@ __device__ __forceinline__ void sclear(uint32_t* p, uint32_t count) {
 template <typename Elem>
 __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, uint32_t sigma, uint64_t deadline_ns,
                             uint64_t t_start, pip_job_stats* st, ResumeState* rs, uint32_t budget,
-                            bool prefetch = false) {
+                            bool prefetch = false, uint64_t slice_ns = 0) {
   __shared__ uint32_t s_cnt[2];
   __shared__ uint32_t s_abort;
+  __shared__ uint32_t s_pause;
+  const uint64_t t_item = (rs != nullptr && slice_ns != 0) ? globaltimer_ns() : 0;
   const uint32_t n = job.n;
   const uint32_t F = job.F;
   const uint32_t ns = sigma * F + 32u;
@@ -201,7 +203,10 @@ __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, 
       if (tid == 0) {
         s_cnt[b] = 0;
         if (nl_next >= m) s_abort = PIP_EINTERNAL;  // no commit: impossible
-        if (globaltimer_ns() - t_start > deadline_ns) s_abort = PIP_ETIMEOUT;
+        const uint64_t now = globaltimer_ns();
+        if (now - t_start > deadline_ns) s_abort = PIP_ETIMEOUT;
+        // a resumable run also pauses once its time slice is used up
+        s_pause = (t_item != 0 && now - t_item >= slice_ns) ? 1u : 0u;
       }
       __syncthreads();
       rounds += 1u;
@@ -221,7 +226,7 @@ __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, 
         status = PIP_EINTERNAL;
         break;
       }
-      if (rs != nullptr && r + 1u >= budget) {
+      if (rs != nullptr && (r + 1u >= budget || s_pause != 0u)) {
         // pause at the round boundary: save the carried losers (buffer nb
         // holds the next round's queue) and the frontier
         for (uint32_t p = tid; p < nl; p += NT) stcg(rs->Q + p, Qnb[p]);

@@ -48,7 +48,7 @@ int64_t now_ns() {
 
 __global__ void __launch_bounds__(1024) serve_tick_kernel(ServeSlot* slots, const uint32_t* work, uint32_t count,
                                                           uint32_t* next, uint32_t fmax, uint32_t sigma,
-                                                          uint32_t budget, uint64_t deadline_ns) {
+                                                          uint32_t budget, uint64_t deadline_ns, uint64_t slice_ns) {
   extern __shared__ uint32_t smem[];
   __shared__ uint32_t s_w;
   const uint64_t t0 = globaltimer_ns();
@@ -61,10 +61,12 @@ __global__ void __launch_bounds__(1024) serve_tick_kernel(ServeSlot* slots, cons
     ServeSlot* sl = slots + work[w];
     const BatchJob job = sl->job;
     uint32_t st;
-    if (sl->elem_bytes == 4) st = run_job<uint32_t>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget);
+    if (sl->elem_bytes == 4)
+      st = run_job<uint32_t>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false, slice_ns);
     else if (sl->elem_bytes == 8)
-      st = run_job<unsigned long long>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget);
-    else st = run_job<uint4>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget);
+      st = run_job<unsigned long long>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false,
+                                       slice_ns);
+    else st = run_job<uint4>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false, slice_ns);
     (void)st;  // the status is in the request's round state
   }
 }
@@ -111,6 +113,7 @@ struct pip_server {
   uint64_t peak_used = 0;
   pip_serve_options opt{};
   uint32_t sigma = 4, fmax = 1024, threads = 512, max_resident = 1024, rounds_per_tick = 128;
+  uint64_t tick_ns = 1000000;
   uint64_t smem = 0;
   uint32_t blocks = 0;
   cudaStream_t stream = nullptr;
@@ -126,6 +129,7 @@ struct pip_server {
   std::vector<pip::Req*> resident;
   std::unordered_map<uint64_t, pip::Req*> reqs;
   std::vector<void*> to_free;  // released server-owned arrays, freed by the loop thread
+  std::deque<uint64_t> finished;  // tickets in completion order, not yet handed out by next_done
   uint64_t next_ticket = 1;
   uint64_t submitted = 0, admitted = 0, completed = 0, ticks = 0;
   bool stop = false;
@@ -209,20 +213,30 @@ void pip_server::loop() {
       }
       cudaMemcpyAsync(d_slots + r->slot, &hs, sizeof(ServeSlot), cudaMemcpyHostToDevice, stream);
     }
-    // one tick over every resident request
+    // one tick over every resident request, the most remaining work first
+    // (the largest requests set the makespan), each for a time slice that
+    // spreads the tick's time budget over the requests per block
     uint32_t count = 0;
     int max_slot = -1;
+    std::vector<std::pair<uint64_t, int>> order;
+    order.reserve(resident.size());
     for (Req* r : resident) {
-      h_work[count++] = (uint32_t)r->slot;
+      const ServeSlot& hs = h_slots[r->slot];
+      const uint64_t left = hs.rs.started ? (uint64_t)hs.rs.L + hs.rs.nl : r->n;
+      order.emplace_back(left, r->slot);
       max_slot = std::max(max_slot, r->slot);
       r->ticks += 1;
     }
+    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    for (const auto& o : order) h_work[count++] = (uint32_t)o.second;
     if (count > 0) {
       cudaMemcpyAsync(d_work, h_work, count * sizeof(uint32_t), cudaMemcpyHostToDevice, stream);
       cudaMemsetAsync(d_next, 0, sizeof(uint32_t), stream);
       const uint32_t grid = std::max(1u, std::min(count, blocks));
+      const uint64_t waves = (count + grid - 1) / grid;
+      const uint64_t slice = std::max<uint64_t>(20000ull, tick_ns / waves);
       serve_tick_kernel<<<grid, threads, smem, stream>>>(d_slots, d_work, count, d_next, fmax, sigma,
-                                                         rounds_per_tick, 120000000000ull);
+                                                         rounds_per_tick, 120000000000ull, slice);
       cudaMemcpyAsync(h_slots, d_slots, (size_t)(max_slot + 1) * sizeof(ServeSlot), cudaMemcpyDeviceToHost, stream);
     }
     const cudaError_t e = cudaStreamSynchronize(stream);
@@ -249,6 +263,7 @@ void pip_server::loop() {
           used -= r->aux_bytes;
           free_slots.push_back(r->slot);
           ++completed;
+          finished.push_back(r->ticket);
           if (r->status != PIP_OK && r->owned) {
             // a failed request keeps no server-owned array; its charge goes back now
             if (r->A != nullptr) cudaFreeAsync(r->A, stream);
@@ -286,7 +301,8 @@ pip_status pip_serve_create(pip_server** out, uint64_t device_budget_bytes, int 
   s->fmax = s->opt.fresh_cap ? s->opt.fresh_cap : 1024u;
   s->threads = s->opt.block_threads ? s->opt.block_threads : 512u;
   s->max_resident = s->opt.max_resident ? s->opt.max_resident : 1024u;
-  s->rounds_per_tick = s->opt.rounds_per_tick ? s->opt.rounds_per_tick : 128u;
+  s->rounds_per_tick = s->opt.rounds_per_tick ? s->opt.rounds_per_tick : 1000000u;
+  s->tick_ns = (uint64_t)(s->opt.tick_us ? s->opt.tick_us : 1000u) * 1000ull;
   if (s->sigma < 2 || s->sigma > 16 || s->threads < 128 || s->threads > 1024 || s->threads % 32 ||
       s->fmax > cta_max_fmax(s->sigma)) {
     delete s;
@@ -313,6 +329,10 @@ pip_status pip_serve_create(pip_server** out, uint64_t device_budget_bytes, int 
     return PIP_EINVAL;
   }
   s->blocks = (uint32_t)per_sm * (uint32_t)di.sms;
+  // by default a request is resident only while a tick block is free for it,
+  // so every resident request advances for the whole tick (requests beyond
+  // that wait in the arrival-ordered admission queue)
+  if (s->opt.max_resident == 0) s->max_resident = s->blocks;
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&s->d_slots, sizeof(ServeSlot) * s->max_resident) != cudaSuccess ||
       cudaMallocHost(&s->h_slots, sizeof(ServeSlot) * s->max_resident) != cudaSuccess ||
@@ -409,6 +429,21 @@ pip_status pip_serve_wait(pip_server* s, uint64_t ticket, uint32_t timeout_ms, v
   if (A_out != nullptr) *A_out = r->A;
   fill_stats(r, st);
   return static_cast<pip_status>(r->status);
+}
+
+pip_status pip_serve_next_done(pip_server* s, uint32_t timeout_ms, uint64_t* ticket) {
+  if (s == nullptr || ticket == nullptr) return PIP_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return !s->finished.empty(); }))
+      return PIP_EAGAIN;
+    const uint64_t t = s->finished.front();
+    s->finished.pop_front();
+    if (s->reqs.count(t)) {  // skip requests released before they were collected here
+      *ticket = t;
+      return PIP_OK;
+    }
+  }
 }
 
 pip_status pip_serve_release(pip_server* s, uint64_t ticket) {

@@ -121,3 +121,15 @@ def test_late_arrivals_overlap_running_requests(pip):
         assert s_short.done_ns < s_long.done_ns
         assert s_long.ticks > 1
         assert np.array_equal(result(pip, srv.poll(short_t)[0], 1 << 12, "u32"), expected(1 << 12, "u32", 2))
+
+
+def test_next_done_returns_completion_order(pip):
+    with pip.Server(8 << 30) as srv:
+        big = srv.submit(1 << 24, "u64", seed=1, eps=0.5)
+        smalls = [srv.submit(1000 + k, "u32", seed=k, eps=0.5) for k in range(20)]
+        got = [srv.next_done() for _ in range(21)]
+        assert sorted(got) == sorted([big] + smalls)
+        assert got[-1] == big  # the long request finishes last
+        for t in got:
+            srv.release(t)
+        assert srv.next_done(timeout_ms=10) is None
