@@ -100,12 +100,10 @@ typedef struct {
 /* Prefetch into L2, one round ahead, the array lines the next fresh block
  * will swap. */
 #define PIP_FLAG_PREFETCH 2u
-/* L2 eviction priorities: the array's lines evict-first, the reservation
- * tables' lines evict-last.  Performance hints only; results are identical. */
-#define PIP_FLAG_ARRAY_EVICT_FIRST 4u
-#define PIP_FLAG_TABLE_EVICT_LAST 8u
-/* Only the array stores are marked evict-first (loads keep the normal policy). */
-#define PIP_FLAG_ARRAY_STORE_EVICT_FIRST 16u
+/* Grid driver: keep the normal L2 eviction priority for the array stores
+ * (by default they are marked evict-first).  Performance only; results are
+ * identical.  (Flag bits 4 and 8 are unused.) */
+#define PIP_FLAG_STORE_EVICT_NORMAL 16u
 /* Driver selection: by default arrays whose prefix fits in one block's shared
  * memory run on one block, larger prefixes on the persistent grid. */
 #define PIP_FLAG_FORCE_GRID 32u

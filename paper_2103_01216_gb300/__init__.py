@@ -177,9 +177,7 @@ class ServeInfo(ctypes.Structure):
 STATS_BYTES = ctypes.sizeof(Stats)
 JOB_STATS_BYTES = ctypes.sizeof(JobStats)
 DRIVER_GRID, DRIVER_CTA, DRIVER_CLUSTER = 0, 1, 2
-FLAG_ARRAY_EVICT_FIRST = 4
-FLAG_TABLE_EVICT_LAST = 8
-FLAG_ARRAY_STORE_EVICT_FIRST = 16
+FLAG_STORE_EVICT_NORMAL = 16
 FLAG_FORCE_GRID = 32
 FLAG_FORCE_CTA = 64
 FLAG_FORCE_CLUSTER = 128

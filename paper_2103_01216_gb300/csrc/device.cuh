@@ -1,6 +1,6 @@
 // Device primitives shared by the round kernels: the swap-target generator,
 // the reservation-slot map, L2-coherent loads/stores and the bounded grid
-// barrier.  sm_103a only.
+// barrier with its per-round counting word.  sm_103a only.
 #pragma once
 
 #include <cstdint>
@@ -48,18 +48,10 @@ __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 template <typename T>
 __device__ __forceinline__ void stcg(T* p, T v) { __stcg(p, v); }
 
-// ---- L2 eviction-priority policies (createpolicy) and hinted accesses.
-// The array A is streamed through L2 once per swap, so its accesses can be
-// marked evict-first; the reservation tables are reused within a round and
-// can be marked evict-last, so that the array does not push them out.
+// ---- L2 eviction-priority policies (createpolicy) and hinted stores.
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ uint64_t policy_evict_normal() {
@@ -68,24 +60,6 @@ __device__ __forceinline__ uint64_t policy_evict_normal() {
   return p;
 }
 
-__device__ __forceinline__ uint32_t ld_hint(const uint32_t* p, uint64_t pol) {
-  uint32_t v;
-  asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned long long ld_hint(const unsigned long long* p, uint64_t pol) {
-  unsigned long long v;
-  asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint4 ld_hint(const uint4* p, uint64_t pol) {
-  uint4 v;
-  asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p), "l"(pol)
-               : "memory");
-  return v;
-}
 __device__ __forceinline__ void st_hint(uint32_t* p, uint32_t v, uint64_t pol) {
   asm volatile("st.global.cg.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
@@ -97,26 +71,30 @@ __device__ __forceinline__ void st_hint(uint4* p, uint4 v, uint64_t pol) {
                "r"(v.z), "r"(v.w), "l"(pol)
                : "memory");
 }
-// Fire-and-forget atomic max (no value returned to the thread).
-__device__ __forceinline__ void red_max_hint(uint32_t* p, uint32_t v, uint64_t pol) {
-  asm volatile("red.relaxed.gpu.global.max.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
-               : "memory");
+// Fire-and-forget atomic max and or (no value returned to the thread).
+__device__ __forceinline__ void red_max(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ uint64_t ld_acquire_u64(const unsigned long long* p) {
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ void red_relaxed_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -131,53 +109,79 @@ __device__ __forceinline__ void set_status(uint32_t* status, uint32_t code) {
 }
 
 // ---------------------------------------------------------------- barrier
-// Bounded grid-wide barrier over `nblocks` co-resident blocks.  `counter` is
-// a monotone 64-bit arrival count: barrier number b (0-based) completes when
-// it reaches (b+1)*nblocks, so it never needs resetting.  Thread 0 of each
-// block arrives with release semantics and waits with acquire loads; the
-// block's bar.sync on either side extends the ordering to all its threads.
-// The wait gives up after `timeout_ns`, or as soon as another block has
-// recorded an error, and the function then returns false (status set) so the
-// caller can leave the kernel; every block then exits at its next barrier.
-// One thread's part of the barrier: arrive (release) unless `arrive` is
-// false, then wait (acquire) for barrier number `epoch` to complete, bounded
-// by `timeout_ns` and by an error recorded elsewhere.  Returns 1 on success.
-__device__ __forceinline__ uint32_t barrier_arrive_wait(unsigned long long* counter, uint32_t nblocks,
-                                                        uint64_t epoch, uint32_t* status, uint64_t timeout_ns,
-                                                        bool arrive) {
-  uint32_t ok = 1;
-  const uint64_t target = (epoch + 1) * (uint64_t)nblocks;
+// Bounded grid-wide barrier through one 64-bit word per round, which also
+// carries per-block sums:
+//   bits  0..9   arriving blocks (at most 1023 blocks),
+//   bits 10..19  blocks that recorded an error during the phase,
+//   bits 20..41  sum of count0 (at most 2^22 - 1),
+//   bits 42..63  sum of count1 (at most 2^22 - 1).
+// Thread 0 of each block publishes the block's work (the bar.sync, then a
+// gpu-scope acq_rel fence: a release) and adds its contribution; it then
+// polls with relaxed loads until the arrival field reaches nblocks and fences
+// again (acquire), and a closing bar.sync hands the ordering to the whole
+// block.  The word must be zero before the first arrival and is reset by the
+// caller once no block can still be polling it.  The wait gives up after
+// `timeout_ns`, or as soon as another block has recorded an error in
+// `status` (recording PIP_ETIMEOUT on a timeout).  `arrive == false` skips
+// the arrival (a test hook that makes every other block's wait run out).
+constexpr uint32_t kBwArriveBits = 10, kBwErrBits = 10, kBwCountBits = 22;
+constexpr uint64_t kBwArriveMask = (1ull << kBwArriveBits) - 1ull;
+constexpr uint32_t kBwMaxBlocks = (1u << kBwArriveBits) - 1u;
+constexpr uint32_t kBwMaxCount = (1u << kBwCountBits) - 1u;
+
+struct RoundSum {
+  uint32_t count0, count1;  // sums over all blocks
+  uint32_t errors;          // blocks that flagged an error
+};
+
+// Thread 0's part: arrive, then wait; returns the completed word, or ~0 when
+// the wait gave up.
+__device__ __forceinline__ unsigned long long round_barrier_wait(unsigned long long* word, uint32_t nblocks,
+                                                                 unsigned long long add, uint32_t* status,
+                                                                 uint64_t timeout_ns, bool arrive) {
   if (arrive) {
-    __threadfence();
-    red_release_add_u64(counter, 1ull);
+    fence_acq_rel_gpu();
+    red_relaxed_add_u64(word, add);
   }
   uint64_t t0 = 0;
   uint32_t polls = 0;
-  while (ld_acquire_u64(counter) < target) {
+  unsigned long long v;
+  while (((v = ld_relaxed_u64(word)) & kBwArriveMask) < nblocks) {
     if ((++polls & 63u) == 0) {
-      if (ld_relaxed_u32(status) != 0u) { ok = 0; break; }
+      if (ld_relaxed_u32(status) != 0u) return ~0ull;
       const uint64_t now = globaltimer_ns();
       if (t0 == 0) t0 = now;
       else if (now - t0 > timeout_ns) {
         set_status(status, PIP_ETIMEOUT);
-        ok = 0;
-        break;
+        return ~0ull;
       }
     }
   }
-  if (ok && ld_relaxed_u32(status) != 0u) ok = 0;
-  return ok;
+  fence_acq_rel_gpu();
+  return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned long long* counter, uint32_t nblocks,
-                                             uint64_t& epoch, uint32_t* status,
-                                             uint64_t timeout_ns, bool arrive = true) {
-  __shared__ uint32_t s_ok;
+// The whole block: bar.sync, thread 0 arrives with (count0, count1, error
+// flag) and waits, then calls on_done(ok, sums) -- ok is false when the wait
+// gave up -- and a closing bar.sync publishes what on_done wrote to shared
+// memory.
+template <typename OnDone>
+__device__ __forceinline__ void round_barrier(unsigned long long* word, uint32_t nblocks, uint32_t count0,
+                                              uint32_t count1, bool err, uint32_t* status, uint64_t timeout_ns,
+                                              bool arrive, OnDone on_done) {
   __syncthreads();
-  if (threadIdx.x == 0) s_ok = barrier_arrive_wait(counter, nblocks, epoch, status, timeout_ns, arrive);
+  if (threadIdx.x == 0) {
+    const unsigned long long add = 1ull + ((unsigned long long)(err ? 1u : 0u) << kBwArriveBits) +
+                                   ((unsigned long long)count0 << (kBwArriveBits + kBwErrBits)) +
+                                   ((unsigned long long)count1 << (kBwArriveBits + kBwErrBits + kBwCountBits));
+    const unsigned long long v = round_barrier_wait(word, nblocks, add, status, timeout_ns, arrive);
+    RoundSum sum;
+    sum.errors = (uint32_t)((v >> kBwArriveBits) & ((1ull << kBwErrBits) - 1ull));
+    sum.count0 = (uint32_t)((v >> (kBwArriveBits + kBwErrBits)) & kBwMaxCount);
+    sum.count1 = (uint32_t)(v >> (kBwArriveBits + kBwErrBits + kBwCountBits));
+    on_done(v != ~0ull, sum);
+  }
   __syncthreads();
-  epoch += 1;
-  return s_ok != 0u;
 }
 
 }  // namespace pip

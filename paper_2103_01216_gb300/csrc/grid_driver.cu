@@ -5,16 +5,20 @@
 // Appendix A.2) with no host round trip.
 //
 // Round r (0-based) has an active set of m_r swaps: the n_r losers carried
-// from round r-1 (queue Q[r&1]) followed by the fresh block W_r = [L_r, L_{r-1})
-// (L_{-1} = n).  Invariant: every unfinished step with index >= L_r is active,
-// which is what makes a commit safe (Section 4.1: always work on the first
-// unfinished swaps in sequential order).
+// from round r-1 and the fresh block W_r = [L_r, L_{r-1}) (L_{-1} = n).
+// Invariant: every unfinished step with index >= L_r is active, which is what
+// makes a commit safe (Section 4.1: always work on the first unfinished swaps
+// in sequential order).  A block keeps the losers it produced in an on-chip
+// list and works on them again in the next round; only those beyond the
+// list's capacity go to an overflow queue in device memory (Q[r&1]), which
+// the next round deals out over all blocks.  Each block also takes one
+// contiguous slice of W_r.
 //
 // The rounds are software-pipelined so that one grid barrier per round
 // suffices.  Between barriers B_{r-1} and B_r, phase P_r
 //   (a) decides round r: step i commits iff no active step targets location i
 //       and i holds the maximum priority on its target; winners swap A[i] and
-//       A[H[i]]; losers are queued for round r+1 and immediately reserve for it;
+//       A[H[i]]; losers are kept for round r+1 and immediately reserve for it;
 //   (b) lets the fresh block W_{r+1} reserve for round r+1;
 //   (c) clears the tables of round r-1 (the cleaning phase of Appendix A.1).
 // Reservations for round r+1 therefore land in a different table (S/D index
@@ -22,21 +26,28 @@
 // ((r+2)%3).
 //
 // Reservation structures of one round (priority of step i is i+1, 0 = unset):
-//   D (dense window, RP-Final): one word per location of W_r, exact
-//     max-priority of the swaps targeting that location.
-//   S (slot table): nslots words; a location t outside W_r maps to slot
-//     slot_of(t) and the word holds the max priority over all swaps whose
-//     target maps there.  Unlike the paper's keyed hash table this table is
-//     keyless, so a slot shared by two targets can make a swap fail although
-//     it had no real conflict.  Such spurious failures only delay a swap: a
-//     swap still commits only if no higher-priority active swap touches either
-//     of its locations, and the highest-priority active swap always commits,
-//     so every round makes progress and the result is the sequential one.
+//   S (slot table): nslots words; target t maps to slot slot_of(t) and the
+//     word holds the max priority over all swaps whose target maps there.
+//     Unlike the paper's keyed hash table this table is keyless, so a slot
+//     shared by two targets can make a swap fail although it had no real
+//     conflict.  Such spurious failures only delay a swap: a swap still
+//     commits only if no higher-priority active swap touches either of its
+//     locations, and the highest-priority active swap always commits, so
+//     every round makes progress and the result is the sequential one.
+//   D (window bitmap, the dense array of RP-Final reduced to one bit per
+//     location): bit t - L_r is set when some active swap targets location
+//     t of the fresh window W_r.  Any swap targeting t has a larger index
+//     than t, so a set bit is exactly "a higher-priority swap targets t".
 // Commit test of active step i with target h != i (OneRes rule, Appendix A.2):
-//   own location free: D[i - L_r] == 0 for fresh i, S[slot(i)] <= i+1 for a
-//     carried loser (every swap targeting i has a higher priority than i);
-//   target won:        (h in W_r ? D[h - L_r] : S[slot(h)]) == i+1.
+//   own location free: bit i - L_r of D clear for fresh i, S[slot(i)] <= i+1
+//     for a carried loser (every swap targeting i has a higher priority);
+//   target won:        S[slot(h)] == i+1.
 // Self-loops (h == i) never reserve and finish at once (text under Alg. 1).
+//
+// Synchronisation: one bounded grid barrier per round through a per-round
+// 64-bit word that also sums the blocks' loser counts and overflow counts, so
+// the next round's active set is known when the barrier completes, with no
+// further load; no global atomic is on the common path of a round.
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -55,15 +66,15 @@ __device__ uint32_t g_error_latch;
 
 namespace {
 
-constexpr uint32_t kLoserBuf = 2048;  // per-block staging of losers (8 KB)
 // Positions per thread in flight in the commit phase, and the launch bounds:
-// 32 registers and 2048 resident threads per SM measured best on GB300 (more
-// warps beat deeper per-thread batches for this random-access mix).
+// two positions per thread with 40 registers (three 512-thread blocks per SM)
+// measured best on GB300; at 32 registers the same loop spills, and one
+// position per thread at four blocks per SM is 2-8 % slower.
 #ifndef PIP_KU
 #define PIP_KU 2
 #endif
 #ifndef PIP_MIN_BLOCKS
-#define PIP_MIN_BLOCKS 4
+#define PIP_MIN_BLOCKS 3
 #endif
 #ifndef PIP_MAX_THREADS
 #define PIP_MAX_THREADS 512
@@ -79,24 +90,19 @@ __device__ __forceinline__ uint32_t target_of(const GridArgs& a, uint32_t i) {
 }
 
 // Reserve target h for step i in the tables of a round whose fresh window is
-// [wlo, whi).
+// [wlo, whi): the priority goes to the slot table, and a target inside the
+// window also sets its bit in the window bitmap.
 __device__ __forceinline__ void reserve(uint32_t* D, uint32_t* S, uint32_t nslots, uint32_t wlo,
-                                        uint32_t whi, uint32_t h, uint32_t prio, uint64_t tpol) {
-  if (h >= wlo && h < whi) red_max_hint(D + (h - wlo), prio, tpol);
-  else red_max_hint(S + slot_of(h, nslots), prio, tpol);
+                                        uint32_t whi, uint32_t h, uint32_t prio) {
+  if (h >= wlo && h < whi) red_or(D + ((h - wlo) >> 5), 1u << ((h - wlo) & 31u));
+  red_max(S + slot_of(h, nslots), prio);
 }
 
-// L2 policies of one thread: for the array and for the reservation tables.
-struct Policies {
-  uint64_t arr, arr_st, tab;
-};
-__device__ __forceinline__ Policies make_policies(uint32_t flags) {
-  Policies p;
-  p.arr = (flags & PIP_FLAG_ARRAY_EVICT_FIRST) ? policy_evict_first() : policy_evict_normal();
-  p.arr_st = (flags & (PIP_FLAG_ARRAY_EVICT_FIRST | PIP_FLAG_ARRAY_STORE_EVICT_FIRST)) ? policy_evict_first()
-                                                                                        : policy_evict_normal();
-  p.tab = (flags & PIP_FLAG_TABLE_EVICT_LAST) ? policy_evict_last() : policy_evict_normal();
-  return p;
+// L2 policy of the array stores.  A stored line (both sides of a swap) is not
+// read again soon, so by default it is marked evict-first, which leaves more
+// of L2 to the reservation tables (measured 4 % faster at n = 10^9).
+__device__ __forceinline__ uint64_t array_store_policy(uint32_t flags) {
+  return (flags & PIP_FLAG_STORE_EVICT_NORMAL) ? policy_evict_normal() : policy_evict_first();
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -108,15 +114,14 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // one round ahead of the commit that reads them.
 template <typename Elem, bool kExplicit>
 __device__ __forceinline__ void reserve_fresh(const GridArgs& a, uint32_t lo, uint32_t hi,
-                                              uint32_t* D, uint32_t* S, uint32_t tid, uint32_t T,
-                                              uint64_t tpol) {
+                                              uint32_t* D, uint32_t* S, uint32_t tid, uint32_t T) {
   const bool pf = (a.flags & PIP_FLAG_PREFETCH) != 0u;
   const Elem* A = static_cast<const Elem*>(a.A);
 #pragma unroll 4
   for (uint32_t i = lo + tid; i < hi; i += T) {
     const uint32_t h = target_of<kExplicit>(a, i);
     if (h != i) {
-      reserve(D, S, a.nslots, lo, hi, h, i + 1, tpol);
+      reserve(D, S, a.nslots, lo, hi, h, i + 1);
       if (pf) {
         prefetch_l2(A + h);
         if ((i & 7u) == 0u || i == lo + tid) prefetch_l2(A + i);
@@ -125,202 +130,273 @@ __device__ __forceinline__ void reserve_fresh(const GridArgs& a, uint32_t lo, ui
   }
 }
 
-__device__ __forceinline__ void clear_words(uint32_t* p, uint32_t count, uint32_t tid, uint32_t T,
-                                            uint64_t tpol) {
+__device__ __forceinline__ void clear_words(uint32_t* p, uint32_t count, uint32_t tid, uint32_t T) {
   // 16-byte stores over the 16-byte aligned body, scalars for the tail
   const uint32_t n4 = count >> 2;
   uint4* p4 = reinterpret_cast<uint4*>(p);
-  for (uint32_t j = tid; j < n4; j += T) st_hint(p4 + j, make_uint4(0, 0, 0, 0), tpol);
-  for (uint32_t j = (n4 << 2) + tid; j < count; j += T) st_hint(p + j, 0u, tpol);
+  for (uint32_t j = tid; j < n4; j += T) stcg(p4 + j, make_uint4(0, 0, 0, 0));
+  for (uint32_t j = (n4 << 2) + tid; j < count; j += T) stcg(p + j, 0u);
 }
+
+// Words of a window bitmap over F locations.
+__host__ __device__ __forceinline__ uint32_t window_words(uint32_t F) { return (F + 31u) >> 5; }
 
 template <typename Elem, bool kExplicit>
 __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel(const GridArgs a) {
-  __shared__ uint32_t s_lbuf[kLoserBuf];
-  __shared__ uint32_t s_lcount, s_flush, s_base;
+  // two on-chip loser lists of a.kloc words: the block's losers of the
+  // previous round (worked on now) and of this round (worked on next)
+  extern __shared__ uint32_t s_loc[];
+  __shared__ uint32_t s_nloc[2];
+  __shared__ uint32_t s_lcount, s_err;
+  // Round state, identical in every block: thread 0 derives it from the
+  // barrier word (kept in shared memory so that nothing but the round index
+  // stays live in registers across the barrier).
+  __shared__ uint32_t s_L, s_Lprev, s_g, s_m, s_stop;
+  // run statistics and the deadline, kept by thread 0 (block 0's are reported)
+  __shared__ unsigned long long s_attempts, s_losers, s_deadline;
+  __shared__ uint32_t s_max_active, s_rounds;
 
   Elem* A = static_cast<Elem*>(a.A);
   Ctrl* ctrl = a.ctrl;
-  const uint32_t T = gridDim.x * blockDim.x;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t NT = blockDim.x;
   const uint32_t lane = threadIdx.x & 31u;
-  uint64_t epoch = 0;
-  const uint64_t t_start = globaltimer_ns();
-  const Policies pol = make_policies(a.flags);
+  // records an error of this call and flags it in the block's next arrival
+  auto fail = [&](uint32_t code) {
+    set_status(&ctrl->status, code);
+    s_err = 1u;
+  };
 
-  if (threadIdx.x == 0) s_lcount = 0;
+  if (threadIdx.x == 0) {
+    s_nloc[0] = 0;
+    s_nloc[1] = 0;
+    s_lcount = 0;
+    s_err = 0;
+    s_attempts = 0;
+    s_losers = 0;
+    s_max_active = 0;
+    s_rounds = 0;
+    s_deadline = globaltimer_ns() + a.deadline_ns;
+    // round 0: no carried losers, fresh block W_0 = [n - f_0, n)
+    s_Lprev = a.n;
+    s_L = a.n - min(a.F, a.n - 1u);
+    s_g = 0;
+    s_m = min(a.F, a.n - 1u);
+    s_stop = 0;
+  }
+  __syncthreads();
   // an invalid explicit target sequence was reported by the validation pass
   if (ld_relaxed_u32(&ctrl->status) != 0u) goto done;
 
-  {
-    // ---- prologue: fresh block W_0 = [n - f_0, n) reserves for round 0
-    uint32_t Lprev = a.n;
-    uint32_t f = min(a.F, a.n - 1u);
-    uint32_t L = a.n - f;
-    uint32_t nl = 0;
-    uint32_t m = f;
-    uint64_t attempts = 0, losers_total = 0;
-    uint32_t max_active = 0, rounds = 0;
-    reserve_fresh<Elem, kExplicit>(a, L, Lprev, a.D[0], a.S[0], tid, T, pol.tab);
-    const bool arrive = !((a.flags & PIP_FLAG_TEST_SKIP_BARRIER) && blockIdx.x == 0);
-    if (!grid_barrier(&ctrl->barrier, gridDim.x, epoch, &ctrl->status, a.timeout_ns, arrive)) goto done;
+  // ---- prologue: W_0 reserves for round 0 (barrier 0 uses word bw[0];
+  // round r's barrier uses bw[(r+1)%3])
+  reserve_fresh<Elem, kExplicit>(a, s_L, a.n, a.D[0], a.S[0], blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+  round_barrier(&ctrl->bw[0], gridDim.x, 0u, 0u, false, &ctrl->status, a.timeout_ns,
+                !((a.flags & PIP_FLAG_TEST_SKIP_BARRIER) && blockIdx.x == 0),
+                [&](bool ok, const RoundSum&) { s_stop = ok ? 0u : 2u; });
+  if (s_stop != 0u) goto done;
 
-    for (uint32_t r = 0;; ++r) {
-      const uint32_t b = r % 3u, b1 = (r + 1u) % 3u, b2 = (r + 2u) % 3u;
-      uint32_t* const Dr = a.D[b];
-      uint32_t* const Sr = a.S[b];
-      uint32_t* const Dn = a.D[b1];
-      uint32_t* const Sn = a.S[b1];
-      uint32_t* const Qin = a.Q[r & 1u];
-      uint32_t* const Qout = a.Q[(r + 1u) & 1u];
-      uint32_t* const cnt_out = &ctrl->cnt[b1];
+  for (uint32_t r = 0;; ++r) {
+    const uint32_t L = s_L, Lprev = s_Lprev, m = s_m;
+    const uint32_t b = r % 3u, b1 = (r + 1u) % 3u, b2 = (r + 2u) % 3u;
+    uint32_t* const Dr = a.D[b];
+    uint32_t* const Sr = a.S[b];
+    uint32_t* const Dn = a.D[b1];
+    uint32_t* const Sn = a.S[b1];
+    const uint32_t* const loc_in = s_loc + (r & 1u) * a.kloc;
+    uint32_t* const loc_out = s_loc + ((r + 1u) & 1u) * a.kloc;
+    uint32_t* const Qout = a.Q[(r + 1u) & 1u];
+    uint32_t* const cnt_out = &ctrl->cnt[b1];
 
-      // next round's fresh block W_{r+1} = [Ln, L); throttled so that
-      // m_{r+1} <= (m_r - 1) + fn <= kmax (at least one swap of round r
-      // commits), which bounds the loser queue; with kmax = 2.5 F the
-      // throttle only acts when more than half a block of losers piles up
-      uint32_t fn = min(a.F, L - 1u);
-      fn = min(fn, a.kmax - m + 1u);
-      const uint32_t Ln = L - fn;
+    // next round's fresh block W_{r+1} = [Ln, L); throttled so that
+    // m_{r+1} <= (m_r - 1) + fn <= kmax (at least one swap of round r
+    // commits), which bounds the loser queue; the throttle only acts when
+    // losers pile up beyond the queue's slack
+    const uint32_t fn = min(min(a.F, L - 1u), a.kmax - m + 1u);
+    const uint32_t Ln = L - fn;
 
-      if (tid == 0) {
-        stcg(&ctrl->cnt[b2], 0u);  // counter of round r+2's losers
-        if (globaltimer_ns() - t_start > a.deadline_ns) set_status(&ctrl->status, PIP_ETIMEOUT);
+    // This block's share of round r's active set, in slots of NT items (one
+    // per thread): first its carried losers (its on-chip list, then a slice
+    // of the overflow queue), then one contiguous slice of W_r.  (Dealing W_r
+    // out grid-wide, W_r[c*T + blockIdx.x*NT + t], measured the same at large
+    // F and 10-25 % slower per round at small F.)
+    const uint32_t nloc = s_nloc[r & 1u];
+    const uint32_t g = s_g;
+    const uint32_t kg = (g + gridDim.x - 1u) / gridDim.x;
+    const uint32_t g0 = min(g, blockIdx.x * kg);
+    const uint32_t nlg = nloc + (min(g, g0 + kg) - g0);  // carried items of this block
+    const uint32_t* const Qg = a.Q[r & 1u] + g0 - nloc;  // item p in [nloc, nlg) is Qg[p]
+    const uint32_t f = Lprev - L;
+    const uint32_t qs = (nlg + NT - 1u) / NT;  // slots of carried items
+    const uint32_t kf = (f + gridDim.x - 1u) / gridDim.x;
+    const uint32_t f0 = min(f, blockIdx.x * kf);
+    const uint32_t nf = min(f, f0 + kf) - f0;
+    const uint32_t nslot = qs + (nf + NT - 1u) / NT;
+
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      // Words no block can still be using: the overflow allocator of round
+      // r+2 (last used in phase r-1) and the barrier word of round r+1 (last
+      // polled at barrier r-1, which every block has left since it arrived
+      // at barrier r).
+      stcg(&ctrl->cnt[b2], 0u);
+      stcg(&ctrl->bw[b2], 0ull);
+      if (globaltimer_ns() > s_deadline) fail(PIP_ETIMEOUT);
+    }
+
+    // ---- (a) commit round r.  Each thread takes kU slots at a time and
+    // issues their loads together so that kU independent memory chains are
+    // in flight per thread.
+    for (uint32_t q0 = 0; q0 < nslot; q0 += kU) {
+      uint32_t ii[kU], hh[kU], own[kU], rh[kU];
+      bool act[kU];
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        const uint32_t q = q0 + (uint32_t)j;
+        ii[j] = 0;
+        if (q < qs) {
+          const uint32_t p = q * NT + threadIdx.x;
+          act[j] = p < nlg;
+          if (act[j]) ii[j] = (p < nloc) ? loc_in[p] : ldcg(Qg + p);
+        } else {
+          const uint32_t o = (q - qs) * NT + threadIdx.x;
+          act[j] = q < nslot && o < nf;
+          ii[j] = L + f0 + o;
+        }
       }
-
-      // ---- (a) commit round r.  Each thread takes kU positions at a time
-      // (p, p+T, ..., p+(kU-1)T) and issues their loads together so that kU
-      // independent memory chains are in flight per thread.
-      for (uint32_t p0 = tid & ~31u; p0 < m; p0 += kU * T) {
-        uint32_t ii[kU], hh[kU], own[kU], rh[kU];
-        bool act[kU];
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        hh[j] = act[j] ? target_of<kExplicit>(a, ii[j]) : 0u;
+        act[j] = act[j] && hh[j] != ii[j];  // self-loops finish at once
+      }
+      Elem x[kU], y[kU];
+      const bool spec = (a.flags & PIP_FLAG_SPECULATE) != 0u;
+      if (spec) {  // array loads issued before the decision (wasted for losers)
 #pragma unroll
         for (int j = 0; j < kU; ++j) {
-          const uint32_t p = p0 + lane + (uint32_t)j * T;
-          act[j] = p < m;
-          ii[j] = 0;
-          if (act[j]) ii[j] = (p < nl) ? ld_hint(Qin + p, pol.tab) : L + (p - nl);
-        }
-#pragma unroll
-        for (int j = 0; j < kU; ++j) {
-          hh[j] = act[j] ? target_of<kExplicit>(a, ii[j]) : 0u;
-          act[j] = act[j] && hh[j] != ii[j];  // self-loops finish at once
-        }
-        Elem x[kU], y[kU];
-        const bool spec = (a.flags & PIP_FLAG_SPECULATE) != 0u;
-        if (spec) {  // array loads issued before the decision (wasted for losers)
-#pragma unroll
-          for (int j = 0; j < kU; ++j) {
-            if (act[j]) {
-              x[j] = ld_hint(A + ii[j], pol.arr);
-              y[j] = ld_hint(A + hh[j], pol.arr);
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < kU; ++j) {
-          own[j] = 0;
-          rh[j] = 0;
           if (act[j]) {
-            const uint32_t i = ii[j], h = hh[j];
-            own[j] = (i < Lprev) ? ld_hint(Dr + (i - L), pol.tab) : ld_hint(Sr + slot_of(i, a.nslots), pol.tab);
-            rh[j] = (h >= L && h < Lprev) ? ld_hint(Dr + (h - L), pol.tab)
-                                          : ld_hint(Sr + slot_of(h, a.nslots), pol.tab);
+            x[j] = ldcg(A + ii[j]);
+            y[j] = ldcg(A + hh[j]);
           }
         }
-        bool win[kU];
+      }
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
-          const uint32_t i = ii[j];
-          // own location free: exact window word unset, or every swap mapping to
-          // the slot of i has a priority at most i+1 (so none targets i)
-          const bool own_free = (i < Lprev) ? (own[j] == 0u) : (own[j] <= i + 1u);
-          win[j] = act[j] && own_free && rh[j] == i + 1u;
-          if (win[j] && !spec) {
-            x[j] = ld_hint(A + ii[j], pol.arr);
-            y[j] = ld_hint(A + hh[j], pol.arr);
-          }
+      for (int j = 0; j < kU; ++j) {
+        own[j] = 0;
+        rh[j] = 0;
+        if (act[j]) {
+          const uint32_t i = ii[j], h = hh[j];
+          own[j] = (i < Lprev) ? ldcg(Dr + ((i - L) >> 5)) : ldcg(Sr + slot_of(i, a.nslots));
+          rh[j] = ldcg(Sr + slot_of(h, a.nslots));
         }
+      }
+      bool win[kU];
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
-          if (win[j]) {
-            st_hint(A + ii[j], y[j], pol.arr_st);
-            st_hint(A + hh[j], x[j], pol.arr_st);
-          }
+      for (int j = 0; j < kU; ++j) {
+        const uint32_t i = ii[j];
+        // own location free: no active swap targets i (window bit clear),
+        // or every swap mapping to the slot of i has a priority at most i+1
+        const bool own_free = (i < Lprev) ? (((own[j] >> ((i - L) & 31u)) & 1u) == 0u) : (own[j] <= i + 1u);
+        win[j] = act[j] && own_free && rh[j] == i + 1u;
+        if (win[j] && !spec) {
+          x[j] = ldcg(A + ii[j]);
+          y[j] = ldcg(A + hh[j]);
         }
+      }
+      const uint64_t stpol = array_store_policy(a.flags);
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
-          const bool lose = act[j] && !win[j];
-          if (lose) reserve(Dn, Sn, a.nslots, Ln, L, hh[j], ii[j] + 1u, pol.tab);
-          const unsigned mask = __ballot_sync(kFull, lose);
-          if (mask) {
-            const int leader = __ffs(mask) - 1;
-            uint32_t wbase = 0;
-            if ((int)lane == leader) wbase = atomicAdd(&s_lcount, (uint32_t)__popc(mask));
-            wbase = __shfl_sync(kFull, wbase, leader);
-            if (lose) {
-              const uint32_t idx = wbase + __popc(mask & ((1u << lane) - 1u));
-              if (idx < kLoserBuf) {
-                s_lbuf[idx] = ii[j];
-              } else {  // staging full: direct append
-                const uint32_t q = atomicAdd(cnt_out, 1u);
-                if (q < a.kmax) st_hint(Qout + q, ii[j], pol.tab);
-                else set_status(&ctrl->status, PIP_EINTERNAL);
-              }
+      for (int j = 0; j < kU; ++j) {
+        if (win[j]) {
+          st_hint(A + ii[j], y[j], stpol);
+          st_hint(A + hh[j], x[j], stpol);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        // losers reserve for round r+1 at once and join the block's next
+        // on-chip list, or the overflow queue once that list is full
+        const bool lose = act[j] && !win[j];
+        if (lose) reserve(Dn, Sn, a.nslots, Ln, L, hh[j], ii[j] + 1u);
+        const unsigned mask = __ballot_sync(kFull, lose);
+        if (mask) {
+          const int leader = __ffs(mask) - 1;
+          uint32_t wbase = 0;
+          if ((int)lane == leader) wbase = atomicAdd(&s_lcount, (uint32_t)__popc(mask));
+          wbase = __shfl_sync(kFull, wbase, leader);
+          const uint32_t idx = wbase + __popc(mask & ((1u << lane) - 1u));
+          const bool spill = lose && idx >= a.kloc;
+          if (lose && !spill) loc_out[idx] = ii[j];
+          const unsigned smask = __ballot_sync(kFull, spill);
+          if (smask) {
+            const int sl = __ffs(smask) - 1;
+            uint32_t qbase = 0;
+            if ((int)lane == sl) qbase = atomicAdd(cnt_out, (uint32_t)__popc(smask));
+            qbase = __shfl_sync(kFull, qbase, sl);
+            if (spill) {
+              const uint32_t q = qbase + __popc(smask & ((1u << lane) - 1u));
+              if (q < a.kmax) stcg(Qout + q, ii[j]);
+              else fail(PIP_EINTERNAL);  // cannot happen: the throttle bounds the losers by kmax
             }
           }
         }
       }
-      // flush the block's staged losers with one global atomic
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const uint32_t c = min(s_lcount, kLoserBuf);
-        s_flush = c;
-        s_base = c ? atomicAdd(cnt_out, c) : 0u;
-        s_lcount = 0;
-      }
-      __syncthreads();
-      if (s_base + s_flush <= a.kmax) {
-        for (uint32_t j = threadIdx.x; j < s_flush; j += blockDim.x) st_hint(Qout + s_base + j, s_lbuf[j], pol.tab);
-      } else if (threadIdx.x == 0) {
-        set_status(&ctrl->status, PIP_EINTERNAL);  // cannot happen: some swap commits every round
-      }
-
-      // ---- (b) fresh block of round r+1 reserves
-      reserve_fresh<Elem, kExplicit>(a, Ln, L, Dn, Sn, tid, T, pol.tab);
-
-      // ---- (c) clean round r-1's tables (they become round r+2's)
-      clear_words(a.S[b2], a.nslots, tid, T, pol.tab);
-      clear_words(a.D[b2], a.F, tid, T, pol.tab);
-
-      if (!grid_barrier(&ctrl->barrier, gridDim.x, epoch, &ctrl->status, a.timeout_ns)) goto done;
-
-      const uint32_t nl_next = ldcg(cnt_out);
-      if (nl_next >= m) {  // no swap committed: impossible (the top active swap always wins)
-        if (tid == 0) set_status(&ctrl->status, PIP_EINTERNAL);
-        break;
-      }
-      rounds = r + 1u;
-      attempts += m;
-      losers_total += nl_next;
-      max_active = max(max_active, m);
-      Lprev = L;
-      L = Ln;
-      nl = nl_next;
-      m = nl_next + fn;
-      if (m == 0u) break;
-      if (m > a.kmax || rounds >= a.max_rounds) {
-        if (tid == 0) set_status(&ctrl->status, PIP_EINTERNAL);
-        break;
-      }
     }
-    if (tid == 0 && a.stats != nullptr) {
-      a.stats->rounds = rounds;
-      a.stats->attempts = attempts;
-      a.stats->losers = losers_total;
-      a.stats->max_active = max_active;
-      a.stats->grid_blocks = gridDim.x;
-    }
+
+    // ---- (b) fresh block of round r+1 reserves
+    reserve_fresh<Elem, kExplicit>(a, Ln, L, Dn, Sn, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+
+    // ---- (c) clean round r-1's tables (they become round r+2's)
+    clear_words(a.S[b2], a.nslots, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+    clear_words(a.D[b2], window_words(a.F), blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+
+    // ---- barrier B_r with this block's losers (all, and those spilled to
+    // the overflow queue); thread 0 turns the sums into the next round's
+    // state, which every block computes identically
+    __syncthreads();  // s_lcount is final
+    const uint32_t lc = s_lcount;
+    const uint32_t spilled = lc > a.kloc ? lc - a.kloc : 0u;
+    round_barrier(&ctrl->bw[b1], gridDim.x, lc, spilled, s_err != 0u, &ctrl->status, a.timeout_ns, true,
+                  [&](bool ok, const RoundSum& sum) {
+                    if (!ok) {
+                      s_stop = 2u;
+                      return;
+                    }
+                    if (sum.errors != 0u) {  // recorded in status by the block that failed
+                      s_stop = 1u;
+                      return;
+                    }
+                    const uint32_t m0 = s_m, L0 = s_L, losers = sum.count0;
+                    const uint32_t fn0 = min(min(a.F, L0 - 1u), a.kmax - m0 + 1u);
+                    if (losers >= m0) {  // no swap committed: impossible (the top active swap wins)
+                      set_status(&ctrl->status, PIP_EINTERNAL);
+                      s_stop = 1u;
+                      return;
+                    }
+                    const uint32_t rr = s_rounds + 1u;
+                    s_rounds = rr;
+                    s_attempts += m0;
+                    s_losers += losers;
+                    s_max_active = max(s_max_active, m0);
+                    const uint32_t mn = losers + fn0;
+                    s_Lprev = L0;
+                    s_L = L0 - fn0;
+                    s_g = sum.count1;
+                    s_m = mn;
+                    s_nloc[(rr & 1u)] = min(s_lcount, a.kloc);
+                    s_lcount = 0;
+                    if (mn == 0u) {
+                      s_stop = 1u;
+                    } else if (mn > a.kmax || rr >= a.max_rounds) {
+                      set_status(&ctrl->status, PIP_EINTERNAL);
+                      s_stop = 1u;
+                    }
+                  });
+    if (s_stop != 0u) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats != nullptr && s_stop == 1u) {
+    a.stats->rounds = s_rounds;
+    a.stats->attempts = s_attempts;
+    a.stats->losers = s_losers;
+    a.stats->max_active = s_max_active;
+    a.stats->grid_blocks = gridDim.x;
   }
 done:
   if (threadIdx.x == 0) {
@@ -382,7 +458,7 @@ pip_status take_error_latch(uint32_t* value) {
   return PIP_OK;
 }
 
-uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t threads) {
+uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t threads, uint32_t kloc) {
   const void* k = select_kernel(elem_bytes, explicit_h);
   if (k == nullptr) return 0;
   DeviceInfo di;
@@ -393,13 +469,14 @@ uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t t
     return 0;
   }
   static std::mutex mu;
-  static std::map<std::tuple<int, const void*, uint32_t>, int> cache;
+  static std::map<std::tuple<int, const void*, uint32_t, uint32_t>, int> cache;
   std::lock_guard<std::mutex> lk(mu);
-  const auto key = std::make_tuple(dev, k, threads);
+  const auto key = std::make_tuple(dev, k, threads, kloc);
   auto it = cache.find(key);
   if (it == cache.end()) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)threads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)threads, (size_t)grid_block_smem(kloc)) !=
+        cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -426,6 +503,7 @@ pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint
     a.D[j] = reinterpret_cast<uint32_t*>(base + plan.off_D[j]);
   }
   for (int j = 0; j < 2; ++j) a.Q[j] = reinterpret_cast<uint32_t*>(base + plan.off_Q[j]);
+  a.kloc = plan.kloc;
   a.ctrl = reinterpret_cast<Ctrl*>(base);
   a.stats = stats;
   a.timeout_ns = plan.timeout_ns;
@@ -443,13 +521,13 @@ pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint
   }
   // every block must be co-resident (the cooperative launch refuses otherwise)
   uint32_t blocks = plan.blocks;
-  const uint32_t maxb = grid_driver_max_blocks(plan.elem_bytes, H != nullptr, plan.threads);
+  const uint32_t maxb = grid_driver_max_blocks(plan.elem_bytes, H != nullptr, plan.threads, plan.kloc);
   if (maxb == 0) return PIP_ECUDA;
-  blocks = std::max(1u, std::min(blocks, maxb));
+  blocks = std::max(1u, std::min({blocks, maxb, kBwMaxBlocks}));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(plan.threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = grid_block_smem(plan.kloc);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

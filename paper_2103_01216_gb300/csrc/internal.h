@@ -12,10 +12,15 @@ namespace pip {
 // 256-byte aligned.  Ctrl words come first so a single memset clears them
 // together with the reservation tables.
 struct Ctrl {
-  uint32_t cnt[3];              // loser counters, rotating by round
+  uint32_t cnt[3];              // loser-queue allocators, rotating by round
   uint32_t status;              // first device-side error of this call
-  unsigned long long barrier;   // monotone arrival counter of the grid barrier
-  uint32_t pad[58];
+  unsigned long long barrier;   // monotone arrival counter (cluster driver)
+  // Per-round barrier words of the grid driver, rotating by round: arriving
+  // blocks, blocks that recorded an error, and the sums of the blocks' losers
+  // and of the losers they could not keep on chip (field layout in
+  // device.cuh).
+  unsigned long long bw[3];
+  uint32_t pad[52];
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is one 256-byte line pair");
 
@@ -33,6 +38,7 @@ struct Plan {
   uint32_t nslots = 0;     // reservation slots per table
   uint32_t blocks = 0;     // persistent grid blocks
   uint32_t threads = 0;    // threads per block
+  uint32_t kloc = 0;       // grid driver: on-chip loser list capacity per block and round
   uint64_t timeout_ns = 0;
   uint64_t deadline_ns = 0;
   uint32_t flags = 0;
@@ -54,8 +60,9 @@ struct GridArgs {
   uint32_t kmax;
   uint32_t nslots;
   uint32_t* S[3];
-  uint32_t* D[3];
-  uint32_t* Q[2];
+  uint32_t* D[3];      // window bitmaps: bit d set when an active swap targets location wlo + d
+  uint32_t* Q[2];      // overflow queues: losers that did not fit their block's on-chip list
+  uint32_t kloc;       // capacity of a block's on-chip loser list (shared memory holds two)
   Ctrl* ctrl;
   pip_stats* stats;    // may be nullptr
   uint64_t timeout_ns;
@@ -168,6 +175,8 @@ pip_status take_error_latch(uint32_t* value);
 
 // Largest co-resident block count for the driver with this element size and
 // block size (cached per device).
-uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t threads);
+uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t threads, uint32_t kloc);
+// Shared memory of one grid-driver block: two on-chip loser lists of kloc words.
+inline uint64_t grid_block_smem(uint32_t kloc) { return 8ull * kloc; }
 
 }  // namespace pip

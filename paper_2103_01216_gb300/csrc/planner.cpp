@@ -30,11 +30,26 @@ constexpr uint32_t kItemsPerThread = 2;  // target positions per thread per roun
 
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Cap on the active set: the fresh block F plus room for 1.5 F carried
-// losers, so the throttle in the driver leaves F untouched unless losers pile
-// up (they are typically a few percent).  Only the used part of the loser
-// queues is ever touched.
-uint32_t kmax_of(uint32_t F) { return (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, (uint64_t)F * 5 / 2 + 2); }
+// Grid driver limits from the barrier word's fields: losers per round (at
+// most kmax = 2.5 F + 2) fit 22 bits, arriving blocks 10 bits.
+constexpr uint32_t kGridMaxF = 1600000;
+constexpr uint32_t kGridMaxBlocks = 1023;
+
+// Cap on the grid driver's active set: 2.5 F.  The driver fixes the next
+// fresh block before the current round's losers are known, so it assumes
+// that all but one of the m active swaps lose: F stays untouched while
+// m - 1 + F <= kmax, i.e. with losers up to 1.5 F (they are 10-25 % of F at
+// slot factors 3-4).  A cap of 1.5 F measured 40 % more rounds at
+// n = 10^9, eps = 0.5.  Only the used part of the loser queues is touched.
+#ifndef PIP_KMAX_NUM
+#define PIP_KMAX_NUM 5
+#endif
+uint32_t kmax_of(uint32_t F) {
+  return (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, (uint64_t)F * PIP_KMAX_NUM / 2 + 2);
+}
+
+// Words of the grid driver's window bitmap over F locations.
+uint64_t window_words(uint32_t F) { return ((uint64_t)F + 31) / 32; }
 
 // Fills the layout fields for a given F and slot factor; returns aux bytes.
 uint64_t layout(Plan* p, uint32_t F, uint32_t slot_factor) {
@@ -49,7 +64,7 @@ uint64_t layout(Plan* p, uint32_t F, uint32_t slot_factor) {
   }
   for (int j = 0; j < 3; ++j) {
     p->off_D[j] = off;
-    off += align_up(4ull * p->F);
+    off += align_up(4ull * window_words(p->F));
   }
   for (int j = 0; j < 2; ++j) {
     p->off_Q[j] = off;
@@ -263,14 +278,46 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
     return PIP_OK;
   }
 
-  // grid: enough threads for ~kItemsPerThread active swaps each, at most what
-  // can be co-resident (a cooperative launch needs every block resident)
-  uint32_t maxb = have_dev ? grid_driver_max_blocks(eb, false, threads) : 0;
-  uint64_t want_blocks = (p.kmax + (uint64_t)threads * kItemsPerThread - 1) / ((uint64_t)threads * kItemsPerThread);
-  if (o.grid_blocks) want_blocks = o.grid_blocks;
-  want_blocks = std::max<uint64_t>(1, want_blocks);
-  if (maxb) want_blocks = std::min<uint64_t>(want_blocks, maxb);
-  p.blocks = (uint32_t)want_blocks;
+  // grid: the per-round counts travel in 22-bit fields of the barrier word
+  // (at most kmax losers), and the arrivals in a 10-bit field
+  if (p.F > kGridMaxF) {
+    layout(&p, kGridMaxF, slot_factor);
+  }
+  // Block size: 256 threads for small prefixes, where more and smaller
+  // blocks shorten a latency-bound round (measured 107 against 116 ms at
+  // n = 10^9, eps = 0.5), 512 for large ones (68.7 against 70.0 ms at
+  // eps = 0.25).
+  if (!o.block_threads) {
+    threads = p.F <= 131072u ? 256u : 512u;
+    p.threads = threads;
+  }
+  // Shape: enough threads for ~kItemsPerThread active swaps each (F plus a
+  // quarter for carried losers) and at least two blocks per SM while each
+  // still gets a warp's worth of items (measured: spreading a round over the
+  // whole GPU shortens it even when blocks have little work), at most what
+  // can be co-resident (a cooperative launch needs every block resident).
+  // Each block keeps its losers in an on-chip list sized for a generous
+  // share of them (overflow goes to the queue in device memory); that shared
+  // memory counts against the aux bound, so F shrinks until everything fits.
+  for (;;) {
+    const uint64_t active_est = (uint64_t)p.F + p.F / 4 + 1;
+    uint64_t want = (active_est + (uint64_t)threads * kItemsPerThread - 1) / ((uint64_t)threads * kItemsPerThread);
+    if (have_dev) want = std::max<uint64_t>(want, std::min<uint64_t>(2ull * di.sms, (active_est + 31) / 32));
+    if (o.grid_blocks) want = o.grid_blocks;
+    want = std::max<uint64_t>(1, std::min<uint64_t>(want, kGridMaxBlocks));
+    // blocks that fit with the largest list first, then the list for them
+    const uint32_t maxb = have_dev ? grid_driver_max_blocks(eb, false, threads, 4096) : 0;
+    if (maxb) want = std::min<uint64_t>(want, maxb);
+    const uint64_t share = ((uint64_t)p.F * 3 / 8 + want - 1) / want;
+    p.kloc = (uint32_t)std::min<uint64_t>(4096, std::max<uint64_t>(32, (share + 31) / 32 * 32));
+    p.blocks = (uint32_t)want;
+    p.smem_bytes = (uint64_t)p.blocks * grid_block_smem(p.kloc);
+    if (p.aux_bytes + p.smem_bytes <= p.aux_bound || p.F <= 1) break;
+    const double ratio = (double)p.aux_bound / (double)(p.aux_bytes + p.smem_bytes);
+    const uint64_t nf = (uint64_t)std::floor((double)p.F * std::min(ratio, 0.999));
+    layout(&p, (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(nf, p.F - 1)), slot_factor);
+  }
+  if (p.aux_bytes + p.smem_bytes > p.aux_bound) return PIP_EINVAL;
 
   uint64_t tmo = o.wait_timeout_ns ? o.wait_timeout_ns : kDefaultTimeoutNs;
   if (const char* e = std::getenv("PIP_WAIT_TIMEOUT_MS")) {
