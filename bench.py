@@ -302,6 +302,8 @@ def run_batch(args):
         bopts["block_threads"] = args.block_threads
     if args.prefix_c:
         bopts["prefix_c"] = args.prefix_c
+    if args.flags:
+        bopts["flags"] = args.flags
     b = pip.Batch(arrays, [int(x) for x in seeds], eps=eps, **bopts)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):

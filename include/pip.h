@@ -88,7 +88,7 @@ typedef struct {
     uint32_t fresh_per_round;  /* explicit F (overrides prefix_c; still clamped by the bound) */
     uint32_t slot_factor;      /* reservation slots per active swap (2..16, default 4) */
     uint32_t grid_blocks;      /* persistent blocks (clamped to what can be co-resident) */
-    uint32_t block_threads;    /* 128..512, multiple of 32 */
+    uint32_t block_threads;    /* multiple of 32: 128..512 for the grid driver, up to 1024 for the others */
     uint64_t wait_timeout_ns;  /* limit of each device-side barrier wait (default 2e9 ns) */
     uint32_t flags;            /* PIP_FLAG_* */
 } pip_options;

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(1024) cta_batch_kernel(const BatchHeader* hdr,
     if (j >= hdr->count) break;
     const BatchJob job = jobs[j];
     const uint32_t st = run_job<Elem>(job, smem, hdr->fmax, hdr->sigma, hdr->deadline_ns, t_start,
-                                      stats != nullptr ? stats + job.slot : nullptr, nullptr, 0u);
+                                      stats != nullptr ? stats + job.slot : nullptr, nullptr, 0u,
+                                      (hdr->flags & PIP_FLAG_PREFETCH) != 0u);
     if (st != 0u && threadIdx.x == 0) {
       set_status(&h->status, st);
       atomicCAS(hdr->latch, 0u, st);
@@ -187,9 +188,8 @@ int prepare_kernel(const void* k, uint32_t threads, uint64_t smem) {
 }  // namespace
 
 uint64_t cta_smem_bytes(uint32_t fmax, uint32_t sigma) {
-  const uint64_t NS = (uint64_t)sigma * fmax + 32u;
-  const uint64_t KMAX = (uint64_t)fmax * 5u / 2u + 2u;
-  return 4ull * (2 * NS + 2ull * fmax + 2 * KMAX);
+  // one slot table, one window bitmap, two loser queues (cta_rounds.cuh)
+  return 4ull * ((uint64_t)cta_table_words(fmax, sigma) + cta_window_words(fmax) + 2ull * cta_kmax(fmax));
 }
 
 uint32_t cta_max_fmax(uint32_t sigma) {

@@ -92,7 +92,7 @@ struct BatchHeader {
   uint32_t count;
   uint32_t fmax;
   uint32_t sigma;
-  uint32_t pad0;
+  uint32_t flags;       // PIP_FLAG_PREFETCH: one-round-ahead loads in every block
   uint64_t deadline_ns;
   uint32_t* latch;
   uint32_t pad[54];
@@ -114,7 +114,7 @@ struct ResumeState {
   uint64_t losers;
   uint32_t max_active;
   uint32_t pad;
-  uint32_t* Q;         // carried-loser queue, at least F*5/2+2 words
+  uint32_t* Q;         // carried-loser queue, at least cta_kmax(F) words
 };
 
 struct BatchLaunch {
@@ -130,7 +130,17 @@ struct BatchLaunch {
   bool any_explicit;
 };
 
-// Block-resident driver (cta_driver.cu).
+// Block-resident driver (cta_driver.cu).  A run with fresh block F keeps at
+// most cta_kmax(F) swaps active: the next fresh block is sized once the
+// round's losers are known, so the cap only leaves F/4 of room for them
+// before the fresh block shrinks.
+__host__ __device__ __forceinline__ uint32_t cta_kmax(uint32_t F) { return F + F / 4u + 2u; }
+__host__ __device__ __forceinline__ uint32_t cta_window_words(uint32_t F) { return (((F + 31u) >> 5) + 3u) & ~3u; }
+// Words of the slot table for fresh blocks up to fmax, a multiple of 4 so
+// that the window bitmap after it stays 16-byte aligned.
+__host__ __device__ __forceinline__ uint32_t cta_table_words(uint32_t fmax, uint32_t sigma) {
+  return (sigma * fmax + 32u + 3u) & ~3u;
+}
 uint64_t cta_smem_bytes(uint32_t fmax, uint32_t sigma);
 uint32_t cta_max_fmax(uint32_t sigma);
 pip_status launch_cta_driver(const BatchLaunch& bl, cudaStream_t stream);

@@ -180,6 +180,7 @@ pip_status pip_batch_prepare(const pip_batch_item* items, const pip_batch_plan* 
   hdr->count = plan->count;
   hdr->fmax = plan->fmax;
   hdr->sigma = plan->slot_factor;
+  hdr->flags = o.flags & PIP_FLAG_PREFETCH;
   hdr->deadline_ns = deadline;
   hdr->latch = error_latch_ptr();
   if (hdr->latch == nullptr) return PIP_ECUDA;

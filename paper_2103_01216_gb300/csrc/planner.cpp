@@ -158,7 +158,7 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
   uint32_t slot_factor = o.slot_factor ? o.slot_factor : kDefaultSlotFactor;
   if (slot_factor < 2 || slot_factor > 16) return PIP_EINVAL;
   uint32_t threads = o.block_threads ? o.block_threads : kDefaultThreads;
-  if (threads < 128 || threads > 512 || threads % 32 != 0) return PIP_EINVAL;
+  if (threads < 128 || threads > 1024 || threads % 32 != 0) return PIP_EINVAL;
   p.threads = threads;
 
   // requested prefix
@@ -258,14 +258,14 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
   if (want_cta) {
     p.driver = kDriverCta;
     p.F = cta_fresh(n, eps, opt, slot_factor, fcap);
-    p.kmax = p.F * 5 / 2 + 2;
+    p.kmax = cta_kmax(p.F);
     p.nslots = slot_factor * p.F + 32;
     p.smem_bytes = cta_job_bytes(p.F, slot_factor);
     p.aux_bytes = sizeof(Ctrl);
     p.blocks = 1;
-    // measured on the eps = 0.75 workload: 512 threads and the one-round-ahead
-    // L2 prefetch of the array lines cut a round from 2.46 to 1.97 us
-    p.threads = o.block_threads ? threads : 512;
+    // one thread per fresh swap up to 1024, so that every fresh swap gets
+    // the one-round-ahead loads (PIP_FLAG_PREFETCH turns them on)
+    p.threads = o.block_threads ? threads : (p.F > 512u ? 1024u : 512u);
     p.flags |= PIP_FLAG_PREFETCH;
     uint64_t tmo = o.wait_timeout_ns ? o.wait_timeout_ns : kDefaultTimeoutNs;
     p.timeout_ns = tmo;
@@ -278,6 +278,8 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
     return PIP_OK;
   }
 
+  // the grid kernel is built for at most 512 threads per block
+  if (o.block_threads > 512) return PIP_EINVAL;
   // grid: the per-round counts travel in 22-bit fields of the barrier word
   // (at most kmax losers), and the arrivals in a 10-bit field
   if (p.F > kGridMaxF) {

@@ -141,7 +141,7 @@ struct pip_server {
 namespace pip {
 namespace {
 
-uint64_t req_aux_bytes(uint32_t F) { return ((uint64_t)F * 5 / 2 + 2) * 4 + sizeof(ServeSlot); }
+uint64_t req_aux_bytes(uint32_t F) { return (uint64_t)cta_kmax(F) * 4 + sizeof(ServeSlot); }
 
 }  // namespace
 }  // namespace pip
@@ -189,7 +189,7 @@ void pip_server::loop() {
         }
       }
       if (ok && r->n >= 2) {
-        if (cudaMallocAsync(reinterpret_cast<void**>(&r->Q), ((uint64_t)r->F * 5 / 2 + 2) * 4, stream) !=
+        if (cudaMallocAsync(reinterpret_cast<void**>(&r->Q), (uint64_t)cta_kmax(r->F) * 4, stream) !=
             cudaSuccess) {
           cudaGetLastError();
           r->Q = nullptr;
