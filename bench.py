@@ -566,6 +566,8 @@ def main():
     ap.add_argument("--tick-us", type=int, default=0)
     ap.add_argument("--fresh-cap", type=int, default=1024)
     ap.add_argument("--no-floor", action="store_true")
+    ap.add_argument("--no-rules", dest="rules", action="store_false",
+                    help="skip the two-reservation rule ablation step")
     ap.add_argument("--no-plain", action="store_true", help="serve: skip the plain FIFO comparison")
     args = ap.parse_args()
 
@@ -685,6 +687,22 @@ def main():
                           "aux_bytes": p_["aux_bytes"], "aux_bound_bytes": p_["aux_bound_bytes"],
                           "roofline_frac": ach / measured_peak_hbm()[0]}
 
+    # reservation-rule ablation (Algorithm 1 as printed: two reservations per
+    # step, against the one-reservation rule of the default path), one step
+    rules = None
+    if args.rules:
+        o2 = dict(opts)
+        o2["flags"] = o2.get("flags", 0) | pip.FLAG_TWO_RES
+        ms2 = time_steps(torch, pip, A, seed, eps, 1, 1, stream, o2)
+        st2 = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device=device)
+        pip.shuffle(A, seed=seed, eps=eps, stats=st2, **o2)
+        pip.check()
+        s2 = pip.read_stats(st2)
+        rules = {"two_reservation": {"ms": ms2[0], "value": n / (ms2[0] / 1e3), "rounds": s2.rounds,
+                                     "loser_fraction": s2.losers / max(1, s2.attempts)},
+                 "one_reservation": {"ms": ms_per_step, "value": value, "rounds": st.rounds,
+                                     "loser_fraction": st.losers / max(1, st.attempts)}}
+
     # bare swap traffic of the same shuffle (scrambles A; nothing reads it after)
     floor = None
     if not args.no_floor:
@@ -734,6 +752,7 @@ def main():
         "rounds": st.rounds,
         "loser_fraction": st.losers / max(1, st.attempts),
         "eps_sweep": sweep,
+        "reservation_rules": rules,
         "random_swap_floor": floor,
         "step_ms": ms,
     }

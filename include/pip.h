@@ -115,6 +115,14 @@ typedef struct {
  * checks instead of after them (one memory round trip less per round, extra
  * loads for the swaps that lose).  Performance only; results are identical. */
 #define PIP_FLAG_SPECULATE 256u
+/* The reservation rule of Algorithm 1 as printed: each step reserves both its
+ * own location and its target, and commits iff it holds the maximum on both.
+ * The default is the one-reservation rule of Appendix A.2 (RP-OneRes: only
+ * the target is reserved, the own location is checked).  Both give the same
+ * winners in every round and the same result; this one costs one more
+ * reservation per step.  Honoured by the grid and one-block drivers (the
+ * planner does not choose the cluster driver under it). */
+#define PIP_FLAG_TWO_RES 512u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {

@@ -182,6 +182,7 @@ FLAG_FORCE_GRID = 32
 FLAG_FORCE_CTA = 64
 FLAG_FORCE_CLUSTER = 128
 FLAG_SPECULATE = 256
+FLAG_TWO_RES = 512
 
 _lock = threading.Lock()
 _lib = None

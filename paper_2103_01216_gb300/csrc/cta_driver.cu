@@ -65,7 +65,7 @@ __global__ void validate_batch_kernel(BatchHeader* hdr, const BatchJob* jobs) {
 template <typename Elem>
 __global__ void __launch_bounds__(1024) cta_single_kernel(const BatchJob job, uint32_t sigma, uint64_t deadline_ns,
                                                          Ctrl* ctrl, pip_stats* stats, uint32_t* latch,
-                                                         uint32_t prefetch) {
+                                                         uint32_t flags) {
   extern __shared__ uint32_t smem[];
   __shared__ pip_job_stats s_st;
   if (ld_relaxed_u32(&ctrl->status) != 0u) {  // invalid explicit targets
@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(1024) cta_single_kernel(const BatchJob job, ui
     return;
   }
   const uint32_t st =
-      run_job<Elem>(job, smem, job.F, sigma, deadline_ns, globaltimer_ns(), &s_st, nullptr, 0u, prefetch != 0u);
+      run_job<Elem>(job, smem, job.F, sigma, deadline_ns, globaltimer_ns(), &s_st, nullptr, 0u,
+                    (flags & PIP_FLAG_PREFETCH) != 0u, 0, (flags & PIP_FLAG_TWO_RES) != 0u);
   if (threadIdx.x == 0) {
     if (st != 0u) {
       set_status(&ctrl->status, st);
@@ -258,8 +259,8 @@ pip_status launch_cta_single(const Plan& plan, void* A, const uint32_t* H, uint6
   job.F = plan.F;
   uint32_t sigma = plan.sigma;
   uint64_t deadline = plan.deadline_ns;
-  uint32_t prefetch = (plan.flags & PIP_FLAG_PREFETCH) ? 1u : 0u;
-  void* args[] = {&job, &sigma, &deadline, &ctrl, &stats, &latch, &prefetch};
+  uint32_t flags = plan.flags & (PIP_FLAG_PREFETCH | PIP_FLAG_TWO_RES);
+  void* args[] = {&job, &sigma, &deadline, &ctrl, &stats, &latch, &flags};
   if (cudaLaunchKernel(k, dim3(1), dim3(plan.threads), args, (size_t)smem, stream) != cudaSuccess) {
     cudaGetLastError();
     return PIP_ECUDA;

@@ -28,6 +28,8 @@
 // Commit test of active step i with target h != i:
 //   own location free: D bit clear for a fresh i, S[slot(i)] <= i+1 for a
 //   carried loser; target won: S[slot(h)] == i+1.  Self-loops finish at once.
+// Under the two-reservation rule (Algorithm 1 as printed) every step also
+// reserves its own location, and the own-location test is S[slot(i)] == i+1.
 //
 // Pipelining (lone arrays): while a round commits, thread t already loads
 // the two array elements of the fresh swap it will take next round,
@@ -59,12 +61,15 @@ __device__ __forceinline__ uint32_t job_target(const BatchJob& j, uint32_t i) {
   return j.H != nullptr ? __ldg(j.H + i) : hashed_target(j.seed, i);
 }
 
-// Reserve target h for step i: the priority in the slot table, and the window
-// bit when h lies in the fresh window [wlo, whi).
+// Reserve target h for step i (priority i+1): the priority in the slot table,
+// and the window bit when h lies in the fresh window [wlo, whi).
+// Under the two-reservation rule of Algorithm 1 the step also reserves its
+// own location i.
 __device__ __forceinline__ void sreserve(uint32_t* D, uint32_t* S, uint32_t ns, uint32_t wlo, uint32_t whi,
-                                         uint32_t h, uint32_t prio) {
+                                         uint32_t i, uint32_t h, bool two) {
   if (h >= wlo && h < whi) atomicOr(D + ((h - wlo) >> 5), 1u << ((h - wlo) & 31u));
-  atomicMax(S + slot_of(h, ns), prio);
+  atomicMax(S + slot_of(h, ns), i + 1u);
+  if (two) atomicMax(S + slot_of(i, ns), i + 1u);
 }
 
 // Zeroes count words at p (16-byte aligned): 16-byte stores, then the tail.
@@ -81,12 +86,14 @@ constexpr uint32_t kClockEvery = 8;
 // Runs the shuffle of one array inside the calling block: to completion when
 // rs is null, else at most `budget` rounds starting from (and saving back to)
 // *rs.  `pipelined` turns on the one-round-ahead loads (and L2 prefetches for
-// fresh swaps beyond the first block-full).  Returns the status (0 = ok).
+// fresh swaps beyond the first block-full); `two` selects the
+// two-reservation rule of Algorithm 1 (commit iff the step holds the
+// maximum on the slots of both its locations).  Returns the status (0 = ok).
 // All control decisions are block-uniform.
 template <typename Elem>
 __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, uint32_t sigma, uint64_t deadline_ns,
                             uint64_t t_start, pip_job_stats* st, ResumeState* rs, uint32_t budget,
-                            bool pipelined = false, uint64_t slice_ns = 0) {
+                            bool pipelined = false, uint64_t slice_ns = 0, bool two = false) {
   __shared__ uint32_t s_cnt[2];
   __shared__ uint32_t s_abort;
   __shared__ uint32_t s_pause;
@@ -144,7 +151,7 @@ __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, 
       const uint32_t f0 = Lprev - L;
       const uint32_t i = (p < f0) ? Lprev - 1u - p : Q_base[p - f0];
       const uint32_t h = job_target(job, i);
-      if (h != i) sreserve(D, S, ns, L, Lprev, h, i + 1u);
+      if (h != i) sreserve(D, S, ns, L, Lprev, i, h, two);
     }
     __syncthreads();
     uint32_t b = 0;  // queue buffer holding the current round's carried losers
@@ -190,9 +197,11 @@ __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, 
             ii[j] = i;
             hh[j] = h;
             if (h != i) {
-              const uint32_t own = (i < Lprev) ? D[(i - L) >> 5] : S[slot_of(i, ns)];
+              const uint32_t own = (i < Lprev && !two) ? D[(i - L) >> 5] : S[slot_of(i, ns)];
               const uint32_t rh = S[slot_of(h, ns)];
-              const bool own_free = (i < Lprev) ? (((own >> ((i - L) & 31u)) & 1u) == 0u) : (own <= i + 1u);
+              const bool own_free = two ? own == i + 1u
+                                    : (i < Lprev) ? (((own >> ((i - L) & 31u)) & 1u) == 0u)
+                                                  : (own <= i + 1u);
               win[j] = own_free && rh == i + 1u;
               lose[j] = !win[j];
             }
@@ -261,7 +270,7 @@ __device__ uint32_t run_job(const BatchJob& job, uint32_t* smem, uint32_t fmax, 
         const uint32_t i = (p < fn) ? L - 1u - p : Qn[p - fn];
         const uint32_t h = (p == tid && p < fn && pipelined && tid < min(F, L - 1u)) ? nh : job_target(job, i);
         if (h != i) {
-          sreserve(D, S, ns, Ln, L, h, i + 1u);
+          sreserve(D, S, ns, Ln, L, i, h, two);
           if (pipelined) {
             if (p == tid && p >= fn) {
               nx = ldcg(A + i);

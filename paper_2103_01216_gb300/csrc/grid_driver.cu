@@ -42,6 +42,9 @@
 //   own location free: bit i - L_r of D clear for fresh i, S[slot(i)] <= i+1
 //     for a carried loser (every swap targeting i has a higher priority);
 //   target won:        S[slot(h)] == i+1.
+// With PIP_FLAG_TWO_RES the rule of Algorithm 1 as printed: every step also
+// reserves its own location, and commits iff it holds the maximum on both
+// slots (the same winners, at the cost of one more reservation per step).
 // Self-loops (h == i) never reserve and finish at once (text under Alg. 1).
 //
 // Synchronisation: one bounded grid barrier per round through a per-round
@@ -89,13 +92,16 @@ __device__ __forceinline__ uint32_t target_of(const GridArgs& a, uint32_t i) {
   else return hashed_target(a.seed, i);
 }
 
-// Reserve target h for step i in the tables of a round whose fresh window is
-// [wlo, whi): the priority goes to the slot table, and a target inside the
-// window also sets its bit in the window bitmap.
+// Reserve target h for step i (priority i+1) in the tables of a round whose
+// fresh window is [wlo, whi): the priority goes to the slot table, and a
+// target inside the window also sets its bit in the window bitmap.  Under
+// the two-reservation rule of Algorithm 1 (PIP_FLAG_TWO_RES) the step also
+// reserves its own location i in the slot table.
 __device__ __forceinline__ void reserve(uint32_t* D, uint32_t* S, uint32_t nslots, uint32_t wlo,
-                                        uint32_t whi, uint32_t h, uint32_t prio) {
+                                        uint32_t whi, uint32_t i, uint32_t h, bool two) {
   if (h >= wlo && h < whi) red_or(D + ((h - wlo) >> 5), 1u << ((h - wlo) & 31u));
-  red_max(S + slot_of(h, nslots), prio);
+  red_max(S + slot_of(h, nslots), i + 1u);
+  if (two) red_max(S + slot_of(i, nslots), i + 1u);
 }
 
 // L2 policy of the array stores.  A stored line (both sides of a swap) is not
@@ -121,7 +127,7 @@ __device__ __forceinline__ void reserve_fresh(const GridArgs& a, uint32_t lo, ui
   for (uint32_t i = lo + tid; i < hi; i += T) {
     const uint32_t h = target_of<kExplicit>(a, i);
     if (h != i) {
-      reserve(D, S, a.nslots, lo, hi, h, i + 1);
+      reserve(D, S, a.nslots, lo, hi, i, h, (a.flags & PIP_FLAG_TWO_RES) != 0u);
       if (pf) {
         prefetch_l2(A + h);
         if ((i & 7u) == 0u || i == lo + tid) prefetch_l2(A + i);
@@ -242,6 +248,7 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
       if (globaltimer_ns() > s_deadline) fail(PIP_ETIMEOUT);
     }
 
+    const bool two = (a.flags & PIP_FLAG_TWO_RES) != 0u;
     // ---- (a) commit round r.  Each thread takes kU slots at a time and
     // issues their loads together so that kU independent memory chains are
     // in flight per thread.
@@ -284,7 +291,7 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
         rh[j] = 0;
         if (act[j]) {
           const uint32_t i = ii[j], h = hh[j];
-          own[j] = (i < Lprev) ? ldcg(Dr + ((i - L) >> 5)) : ldcg(Sr + slot_of(i, a.nslots));
+          own[j] = (i < Lprev && !two) ? ldcg(Dr + ((i - L) >> 5)) : ldcg(Sr + slot_of(i, a.nslots));
           rh[j] = ldcg(Sr + slot_of(h, a.nslots));
         }
       }
@@ -294,7 +301,10 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
         const uint32_t i = ii[j];
         // own location free: no active swap targets i (window bit clear),
         // or every swap mapping to the slot of i has a priority at most i+1
-        const bool own_free = (i < Lprev) ? (((own[j] >> ((i - L) & 31u)) & 1u) == 0u) : (own[j] <= i + 1u);
+        // (two-reservation rule: the step holds the maximum on its own slot)
+        const bool own_free = two ? own[j] == i + 1u
+                              : (i < Lprev) ? (((own[j] >> ((i - L) & 31u)) & 1u) == 0u)
+                                            : (own[j] <= i + 1u);
         win[j] = act[j] && own_free && rh[j] == i + 1u;
         if (win[j] && !spec) {
           x[j] = ldcg(A + ii[j]);
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
         // losers reserve for round r+1 at once and join the block's next
         // on-chip list, or the overflow queue once that list is full
         const bool lose = act[j] && !win[j];
-        if (lose) reserve(Dn, Sn, a.nslots, Ln, L, hh[j], ii[j] + 1u);
+        if (lose) reserve(Dn, Sn, a.nslots, Ln, L, ii[j], hh[j], two);
         const unsigned mask = __ballot_sync(kFull, lose);
         if (mask) {
           const int leader = __ffs(mask) - 1;

@@ -232,9 +232,11 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
       }
     }
   }
-  const bool want_cluster =
-      cl_cs != 0 && ((o.flags & PIP_FLAG_FORCE_CLUSTER) || (!forced && !want_cta && !grid_large));
+  const bool want_cluster = cl_cs != 0 && !(o.flags & PIP_FLAG_TWO_RES) &&
+                            ((o.flags & PIP_FLAG_FORCE_CLUSTER) || (!forced && !want_cta && !grid_large));
   if (o.flags & PIP_FLAG_FORCE_CLUSTER && cl_cs == 0) return PIP_EINVAL;
+  // the cluster driver implements the one-reservation rule only
+  if ((o.flags & PIP_FLAG_TWO_RES) && (o.flags & PIP_FLAG_FORCE_CLUSTER)) return PIP_EINVAL;
   if (want_cluster) {
     p.driver = kDriverCluster;
     p.F = F_cl;

@@ -24,8 +24,9 @@ def pip():
     return load_pip()
 
 
-# the three round drivers: persistent grid, one block, one cluster (DSMEM tables)
-DRIVERS = {"grid": 32, "cta": 64, "cluster": 128}
+# the three round drivers: persistent grid, one block, one cluster (DSMEM tables),
+# and the first two under the two-reservation rule of Algorithm 1 as printed
+DRIVERS = {"grid": 32, "cta": 64, "cluster": 128, "grid_tworeserve": 32 | 512, "cta_tworeserve": 64 | 512}
 
 
 def expect_hashed(arr, seed):
@@ -118,7 +119,7 @@ def test_sattolo_targets(pip, n):
 @pytest.mark.parametrize("driver", sorted(DRIVERS))
 @pytest.mark.parametrize("n,F", [(1000, 1), (1000, 64), (65537, 256), (300007, 3000), (1 << 20, 100000)])
 def test_random_explicit_targets(pip, n, F, driver):
-    if driver == "cta" and F > 3000:
+    if driver.startswith("cta") and F > 3000:
         pytest.skip("prefix larger than one block's shared memory")
     H = workloads.random_targets(n, rng_seed=n + F)
     arr = workloads.iota(n, "u64")
@@ -186,6 +187,10 @@ def test_output_does_not_depend_on_launch_shape(pip):
         dict(flags=DRIVERS["cluster"], fresh_per_round=7, block_threads=256),
         dict(flags=DRIVERS["grid"] | 256, fresh_per_round=3000),
         dict(flags=DRIVERS["grid"] | 256, fresh_per_round=50000),
+        dict(flags=512),
+        dict(flags=DRIVERS["grid_tworeserve"], fresh_per_round=50000, slot_factor=2),
+        dict(flags=DRIVERS["cta_tworeserve"], fresh_per_round=700),
+        dict(flags=DRIVERS["cta_tworeserve"] | 2, fresh_per_round=2000, block_threads=1024),
     ]
     for c in configs:
         out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5, **c)
