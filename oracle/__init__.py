@@ -1,13 +1,14 @@
-"""CPU oracle for the parallel in-place random permutation.
+"""CPU oracle for the parallel in-place random permutation and list contraction.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  The product library never links, loads or calls it, and it shares no
 code with the CUDA path (see ``knuth.c`` for the arithmetic, written out from
-Section 4.1 of the paper and from the published SplitMix64 definition).
+Section 4.1 of the paper and from the published SplitMix64 definition, and
+``listc.c`` for list contraction, Section 4.2).
 
-The C part (``knuth.c``) is compiled with the host C compiler into
-``_liboracle.so`` next to this file; :func:`build` does that and
+The C part (``knuth.c``, ``listc.c``) is compiled with the host C compiler
+into ``_liboracle.so`` next to this file; :func:`build` does that and
 :func:`lib` loads it.
 """
 from __future__ import annotations
@@ -20,7 +21,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "knuth.c")
+_SRCS = [os.path.join(_HERE, "knuth.c"), os.path.join(_HERE, "listc.c")]
 _SO = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -29,11 +30,11 @@ ELEM_BYTES = {"u32": 4, "u64": 8, "rec128": 16}
 
 
 def build(force: bool = False) -> str:
-    """Compile ``knuth.c`` into ``_liboracle.so`` (plain C, -O2, no CPU-specific flags)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+    """Compile the C sources into ``_liboracle.so`` (plain C, -O2, no CPU-specific flags)."""
+    if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in _SRCS):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, *_SRCS])
     os.replace(tmp, _SO)
     return _SO
 
@@ -59,6 +60,12 @@ def lib() -> ctypes.CDLL:
             L.oracle_knuth_explicit.restype = ctypes.c_int
             L.oracle_perm_histogram.argtypes = [u32, u64, u64, vp]
             L.oracle_perm_histogram.restype = ctypes.c_int
+            L.oracle_list_contract.argtypes = [vp, u64]
+            L.oracle_list_contract.restype = ctypes.c_int
+            L.oracle_list_check.argtypes = [vp, u64]
+            L.oracle_list_check.restype = ctypes.c_int
+            L.oracle_list_nearest_larger.argtypes = [vp, u64, vp]
+            L.oracle_list_nearest_larger.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -130,3 +137,39 @@ def perm_histogram(n: int, count: int, seed_stride: int) -> np.ndarray:
     if rc != 0:
         raise ValueError("n must be in [1, 10]")
     return counts
+
+
+# ------------------------------------------------------------------ list contraction
+NIL = 0xFFFFFFFFFFFFFFFF
+
+
+def _records(rec) -> np.ndarray:
+    rec = np.asarray(rec)
+    if rec.dtype != np.uint64 or rec.ndim != 2 or rec.shape[1] != 2 or not rec.flags["C_CONTIGUOUS"]:
+        raise ValueError("records must be a C-contiguous (n, 2) uint64 array of (prev, next)")
+    return rec
+
+
+def list_contract(rec: np.ndarray) -> np.ndarray:
+    """Contract every node of the lists in ``rec`` in place (Section 4.2): each
+    record ends up holding the neighbours its node had when spliced out."""
+    rec = _records(rec)
+    if lib().oracle_list_contract(rec.ctypes.data, rec.shape[0]) != 0:
+        raise ValueError("pointer out of range")
+    return rec
+
+
+def list_check(rec: np.ndarray) -> int:
+    """0 when ``rec`` holds valid acyclic doubly-linked lists, else a negative code."""
+    rec = _records(rec)
+    return int(lib().oracle_list_check(rec.ctypes.data, rec.shape[0]))
+
+
+def list_nearest_larger(rec: np.ndarray) -> np.ndarray:
+    """For every node, the nearest node with a larger index before and after it
+    in its list (NIL if none), as an (n, 2) array."""
+    rec = _records(rec)
+    out = np.empty_like(rec)
+    if lib().oracle_list_nearest_larger(rec.ctypes.data, rec.shape[0], out.ctypes.data) != 0:
+        raise MemoryError("oracle_list_nearest_larger")
+    return out

@@ -1,4 +1,5 @@
-"""Round-by-round simulator of the parallel Knuth shuffle (debugging aid).
+"""Round-by-round simulators of the parallel Knuth shuffle and of parallel
+list contraction (debugging aids).
 
 TEST INFRASTRUCTURE ONLY (same rule as the rest of ``oracle/``).
 
@@ -84,3 +85,36 @@ def simulate(A, H, k: int | None = None, rule: str = "oneres", skip_self_loops: 
         # pack the leftovers, keeping sequential order, ahead of the untouched rest
         unfinished = [s for s in prefix if s not in won] + rest
     return A, rounds
+
+
+def list_rounds(rec, k: int | None = None):
+    """Algorithm 2 (Section 4.2) under deterministic reservations.
+
+    rec: list of [prev, next] pairs over nodes 0..n-1 (None marks a list end);
+    node i has priority i.  Each round works on the first ``k`` uncontracted
+    nodes in priority order (None = all of them); every one that is a local
+    minimum of the remaining lists (both current neighbours absent or larger)
+    is marked, then all marked nodes are spliced out together.  A contracted
+    node keeps the neighbours it had when spliced out.  Returns (records,
+    list of per-round contracted sets).
+    """
+    rec = [list(r) for r in rec]
+    n = len(rec)
+    todo = list(range(n))
+    rounds = []
+    while todo:
+        active = todo if k is None else todo[:k]
+        marked = [i for i in active
+                  if (rec[i][0] is None or rec[i][0] > i) and (rec[i][1] is None or rec[i][1] > i)]
+        if not marked:
+            raise RuntimeError("no local minimum among the active nodes (a cycle?)")
+        for i in marked:
+            p, q = rec[i]
+            if p is not None:
+                rec[p][1] = q
+            if q is not None:
+                rec[q][0] = p
+        done = set(marked)
+        todo = [i for i in todo if i not in done]
+        rounds.append(done)
+    return rec, rounds

@@ -93,7 +93,8 @@ def _pins_pass(L):
             return False
     n = 50
     A = np.arange(n, dtype=np.uint64)
-    L.oracle_knuth_explicit(A.ctypes.data, n, 8, np.zeros(n, dtype=np.uint32).ctypes.data)
+    zeros = np.zeros(n, dtype=np.uint32)  # kept alive while the C call reads it
+    L.oracle_knuth_explicit(A.ctypes.data, n, 8, zeros.ctypes.data)
     if A.tolist() != [(i + 1) % n for i in range(n)]:
         return False
     # hashed path: a permutation, and the same one the explicit path gives
@@ -104,7 +105,8 @@ def _pins_pass(L):
     a = np.arange(n, dtype=np.uint64)
     L.oracle_knuth_hash(a.ctypes.data, n, 8, 2)
     b = np.arange(n, dtype=np.uint64)
-    L.oracle_knuth_explicit(b.ctypes.data, n, 8, H.astype(np.uint32).ctypes.data)
+    H32 = H.astype(np.uint32)  # kept alive while the C call reads it
+    L.oracle_knuth_explicit(b.ctypes.data, n, 8, H32.ctypes.data)
     if not np.array_equal(a, b) or not np.array_equal(np.sort(a), np.arange(n, dtype=np.uint64)):
         return False
     # uniformity of H[i]/(i+1): the mean of the normalised target is 1/2
@@ -129,3 +131,65 @@ def test_planted_mistake_is_caught(name, tmp_path):
     assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
     L = _compile(text.replace(old, new), str(tmp_path / f"{name}.so"))
     assert not _pins_pass(L), f"pins did not catch mutation {name}"
+
+
+# ------------------------------------------------------------------ list contraction
+LIST_SRC = os.path.join(ROOT, "oracle", "listc.c")
+LIST_NIL = 0xFFFFFFFFFFFFFFFF
+
+LIST_MUTATIONS = {
+    "splice_writes_wrong_field": ("rec[2 * p + 1] = q;", "rec[2 * p] = q;"),
+    "drops_successor_update": ("rec[2 * q] = p;       /* the successor now skips node i */", ""),
+    "contracts_in_reverse_order": (
+        "for (uint64_t i = 0; i < n; ++i) {\n        const uint64_t p = rec[2 * i], q = rec[2 * i + 1];\n"
+        "        if (p != ORACLE_NIL) {\n            if (p >= n) return -1;",
+        "for (uint64_t i = n; i-- > 0;) {\n        const uint64_t p = rec[2 * i], q = rec[2 * i + 1];\n"
+        "        if (p != ORACLE_NIL) {\n            if (p >= n) return -1;"),
+    "successor_gets_successor": ("rec[2 * q] = p;", "rec[2 * q] = q;"),
+}
+
+
+def _compile_list(src_text, path):
+    c = path + ".c"
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", path, c])
+    L = ctypes.CDLL(path)
+    L.oracle_list_contract.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    L.oracle_list_contract.restype = ctypes.c_int
+    return L
+
+
+def _list_pins_pass(L):
+    """Brute force over every list order for n <= 5 against the nearest-larger
+    definition, and the ascending closed form."""
+    for n in range(1, 6):
+        for order in itertools.permutations(range(n)):
+            rec = np.full((n, 2), LIST_NIL, dtype=np.uint64)
+            for k in range(1, n):
+                rec[order[k], 0] = order[k - 1]
+                rec[order[k - 1], 1] = order[k]
+            if L.oracle_list_contract(rec.ctypes.data, n) != 0:
+                return False
+            for k, v in enumerate(order):
+                left = next((order[j] for j in range(k - 1, -1, -1) if order[j] > v), LIST_NIL)
+                right = next((order[j] for j in range(k + 1, n) if order[j] > v), LIST_NIL)
+                if int(rec[v, 0]) != left or int(rec[v, 1]) != right:
+                    return False
+    return True
+
+
+def test_real_list_oracle_passes_compact_pins(tmp_path):
+    with open(LIST_SRC) as f:
+        L = _compile_list(f.read(), str(tmp_path / "real_list.so"))
+    assert _list_pins_pass(L)
+
+
+@pytest.mark.parametrize("name", sorted(LIST_MUTATIONS))
+def test_planted_list_mistake_is_caught(name, tmp_path):
+    old, new = LIST_MUTATIONS[name]
+    with open(LIST_SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    L = _compile_list(text.replace(old, new), str(tmp_path / f"{name}.so"))
+    assert not _list_pins_pass(L), f"pins did not catch mutation {name}"

@@ -8,7 +8,9 @@ CUDA package, so both sides can take their inputs from here.
 
 The paper measures on synthetic arrays of 10 million to 1 billion 64-bit
 integers (Section 7.2); the shapes below follow that: A[i] = i keys of 4 or 8
-bytes, and 16-byte records {key = i, payload = mix(i)}.
+bytes, and 16-byte records {key = i, payload = mix(i)}.  For list contraction
+it uses 10 to 200 million nodes of two 64-bit pointers (Section 7.3): random
+doubly-linked lists over node ids 0..n-1, NIL = 2^64 - 1 at the ends.
 """
 from __future__ import annotations
 
@@ -104,3 +106,30 @@ def serve_workload(count: int = 20000, lo_exp: int = 12, hi_exp: int = 28, size_
     gaps = -np.log1p(-u) / rate_per_s
     arrivals = np.cumsum(gaps)
     return sizes, dtypes, seeds, arrivals
+
+
+LIST_NIL = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def lists_from_order(order: np.ndarray, nlists: int = 1) -> np.ndarray:
+    """(n, 2) uint64 records (prev, next) of the lists that visit the node ids
+    of ``order`` in turn, cut into ``nlists`` lists of near-equal length."""
+    order = np.asarray(order, dtype=np.uint64)
+    n = order.shape[0]
+    rec = np.full((n, 2), LIST_NIL, dtype=np.uint64)
+    if n == 0:
+        return rec
+    cuts = np.linspace(0, n, max(1, min(nlists, n)) + 1).astype(np.int64)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        seg = order[a:b]
+        if seg.shape[0] > 1:
+            rec[seg[1:], 0] = seg[:-1]
+            rec[seg[:-1], 1] = seg[1:]
+    return rec
+
+
+def random_lists(n: int, rng_seed: int, nlists: int = 1) -> np.ndarray:
+    """Records of ``nlists`` random lists over 0..n-1: the visiting order is a
+    uniform permutation from numpy's PCG64 seeded with ``rng_seed``."""
+    order = np.random.default_rng(rng_seed).permutation(n).astype(np.uint64)
+    return lists_from_order(order, nlists)
