@@ -407,6 +407,87 @@ def run_floor(args):
     return 0
 
 
+LIST_BYTES_PER_NODE = 144  # own 16-byte record read, two random 8-byte writes (32-B sector read + written each)
+PAPER_LIST_PIP_200M_MS = 418.0  # PIP list contraction, 200M nodes, 72 cores + HT (Table "lt-runtime")
+
+
+def run_list(args):
+    """List contraction (Section 4.2, Algorithm 2): n nodes of two 64-bit
+    pointers forming one random doubly-linked list (the paper's workload
+    shape, 10 to 200 million nodes), node i contracting once both current
+    neighbours are larger.  The list is rebuilt before every step (outside the
+    timed region) because contraction consumes it; the order comes from
+    torch.randperm with a fixed seed, and the output of the last step is
+    checked on a sample against the nearest-larger definition."""
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    n, eps = args.n, args.eps
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(args.seed)
+    order = torch.randperm(n, device="cuda", generator=gen)
+    base = torch.full((n, 2), -1, dtype=torch.int64, device="cuda")
+    base[order[1:], 0] = order[:-1]
+    base[order[:-1], 1] = order[1:]
+    nodes = torch.empty_like(base)
+    opts = {}
+    if args.fresh:
+        opts["fresh_per_round"] = args.fresh
+    if args.block_threads:
+        opts["block_threads"] = args.block_threads
+    plan = pip.list_plan(n, eps, **opts)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        nodes.copy_(base)
+        pip.list_contract(nodes, eps=eps, **opts)
+    pip.check()
+    times = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            nodes.copy_(base)
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            pip.list_contract(nodes, eps=eps, **opts)
+            e_.record(stream)
+            e_.synchronize()
+            times.append(s_.elapsed_time(e_))
+    pip.check()
+    st_buf = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    nodes.copy_(base)
+    pip.list_contract(nodes, eps=eps, stats=st_buf, **opts)
+    pip.check()
+    st = pip.read_stats(st_buf)
+    # sampled check: every neighbour at contraction is larger, and one node per
+    # list (the maximum) is left with none
+    out = nodes[::max(1, n // 100000)].cpu()
+    idx = torch.arange(0, n, max(1, n // 100000))
+    ok_larger = bool(torch.all((out == -1) | (out > idx[:, None])))
+    ms = sorted(times)[len(times) // 2]
+    ach = LIST_BYTES_PER_NODE * n / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    line = {
+        "metric": "contracted list nodes/s", "value": n / (ms / 1e3), "unit": "nodes/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"list_contraction_n{n}_one_random_list_eps{eps}", "n": n, "eps": eps,
+                   "record": "2 x 64-bit pointers", "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_node": LIST_BYTES_PER_NODE},
+        "plan": {k: plan[k] for k in ("fresh_per_round", "max_active", "grid_blocks", "block_threads", "aux_bytes",
+                                      "smem_bytes", "aux_bound_bytes", "min_rounds")},
+        "rounds": st.rounds, "carried_fraction": st.losers / max(1, st.attempts),
+        "sample_check": ok_larger,
+        "paper_context": {"pip_72cores_ht_200M_ms": PAPER_LIST_PIP_200M_MS},
+        "gpu_launches": args.steps, "clocks": clk.summary(), "step_ms": times,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _percentile(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -558,7 +639,7 @@ def main():
     ap.add_argument("--grid-blocks", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--flags", type=int, default=0, help="PIP_FLAG_* bits (2 = L2 prefetch of the next block)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "floor"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "floor", "list"])
     ap.add_argument("--batch-count", type=int, default=8192)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--requests", type=int, default=1000)
@@ -579,6 +660,10 @@ def main():
         return run_serve(args)
     if args.workload == "floor":
         return run_floor(args)
+    if args.workload == "list":
+        if args.n == 10**9:
+            args.n = 2 * 10**8  # the paper's largest list
+        return run_list(args)
 
     import torch
 

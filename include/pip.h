@@ -395,6 +395,53 @@ pip_status pip_shuffle_noalloc(void *A_dev, uint64_t n, pip_dtype dtype, uint64_
  */
 pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed, void *stream);
 
+/* ------------------------------------------------------------ list contraction */
+
+/* One node of a doubly-linked list (16 bytes): the indices of its neighbours,
+ * PIP_LIST_NIL at the ends of a list. */
+typedef struct {
+    uint64_t prev;
+    uint64_t next;
+} pip_list_node;
+#define PIP_LIST_NIL 0xFFFFFFFFFFFFFFFFull
+
+/*
+ * pip_list_contract -- in-place list contraction (Section 4.2, Algorithm 2),
+ * made relaxed-PIP by the Decomposable Property: every round works on about
+ * C * n^(1-eps) nodes, so the device scratch stays within
+ * PIP_AUX_C * n^(1-eps) + 4096 bytes (no array indexed by node).
+ *   nodes_dev: device array of n records (16-byte aligned) describing any
+ *              number of acyclic doubly-linked lists over the nodes 0..n-1.
+ *   n        : node count, n < 2^32 - 1.  n <= 1 is a no-op.
+ * Node i has priority i.  Every node is spliced out of its list once both of
+ * its current neighbours are NIL or larger (all local minima of a round at
+ * once), and keeps in its record the two neighbours it had at that moment:
+ * on return, record i holds the nearest nodes with a larger index before and
+ * after i in its original list (PIP_LIST_NIL where there is none) -- the tree
+ * edges of the contraction.  The result equals splicing the nodes out one at
+ * a time in index order.
+ * Errors: an inconsistent input (pointer out of range, prev/next mismatch)
+ * is found by a validation kernel before anything is modified and reported
+ * as PIP_EINVAL by pip_check(); a cycle is detected when a round contracts
+ * nothing and reported as PIP_EINTERNAL (the records are then unspecified).
+ * Scratch is allocated with cudaMallocAsync on `stream` and freed the same way.
+ */
+pip_status pip_list_contract(pip_list_node *nodes_dev, uint64_t n, double eps, void *stream);
+
+/* pip_list_contract_ex -- the same with overrides (opt: prefix_c,
+ * fresh_per_round, grid_blocks, block_threads up to 512, wait_timeout_ns),
+ * caller-provided scratch (aux_dev of at least pip_list_plan's aux_bytes,
+ * 256-byte aligned, or NULL) and a device pip_stats the kernel fills (or
+ * NULL; attempts counts active nodes over all rounds, losers the nodes
+ * carried to a next round). */
+pip_status pip_list_contract_ex(pip_list_node *nodes_dev, uint64_t n, double eps, const pip_options *opt,
+                                void *aux_dev, uint64_t aux_bytes, pip_stats *stats_dev, void *stream);
+
+/* pip_list_plan -- the plan pip_list_contract_ex would use (host only):
+ * elem_bytes = 16, fresh_per_round, max_active, grid_blocks, block_threads,
+ * aux_bytes, smem_bytes, aux_bound_bytes, min_rounds; driver = 3. */
+pip_status pip_list_plan(uint64_t n, double eps, const pip_options *opt, pip_plan_info *out);
+
 /* pip_status_string -- static English description of a status code. */
 const char *pip_status_string(pip_status s);
 

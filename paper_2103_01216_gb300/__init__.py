@@ -248,6 +248,12 @@ def lib() -> ctypes.CDLL:
         L.pip_serve_info_get.restype = i32
         L.pip_serve_destroy.argtypes = [vp]
         L.pip_serve_destroy.restype = i32
+        L.pip_list_contract.argtypes = [vp, u64, dbl, vp]
+        L.pip_list_contract.restype = i32
+        L.pip_list_contract_ex.argtypes = [vp, u64, dbl, ctypes.POINTER(Options), vp, u64, vp, vp]
+        L.pip_list_contract_ex.restype = i32
+        L.pip_list_plan.argtypes = [u64, dbl, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
+        L.pip_list_plan.restype = i32
         _lib = L
         return L
 
@@ -535,3 +541,40 @@ def calibrate_swap_floor(A, seed: int = 0, stream=None) -> None:
     a shuffle of ``A`` with no conflict resolution; leaves ``A`` unspecified."""
     _raise(lib().pip_calibrate_swap_floor(A.data_ptr(), A.shape[0], tensor_dtype(A), seed, _stream_handle(stream)),
            "pip_calibrate_swap_floor")
+
+
+# ------------------------------------------------------------------ list contraction
+LIST_NIL = 0xFFFFFFFFFFFFFFFF
+DRIVER_LIST = 3
+
+
+def list_plan(n: int, eps: float, **options) -> dict:
+    """The plan pip_list_contract_ex would use (host only)."""
+    info = PlanInfo()
+    o = make_options(**options)
+    _raise(lib().pip_list_plan(n, eps, _opt_ptr(o), ctypes.byref(info)), "pip_list_plan")
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+
+def list_contract(nodes, eps: float = 0.5, *, stream=None, aux=None, stats=None, **options) -> None:
+    """Contract every node of the doubly-linked lists in ``nodes`` in place
+    (asynchronous on ``stream``).
+
+    ``nodes``: contiguous CUDA tensor of shape (n, 2) with 8-byte elements
+    (int64 or uint64 bit patterns) holding (prev, next) node indices, -1 /
+    2^64-1 at list ends.  On return row i holds the nearest nodes with a
+    larger index before and after i in its original list.  ``aux``, ``stats``
+    and the keyword options are as in :func:`shuffle`.
+    """
+    if not nodes.is_cuda or not nodes.is_contiguous() or nodes.dim() != 2 or nodes.shape[1] != 2 \
+            or nodes.element_size() != 8:
+        raise ValueError("nodes must be a contiguous (n, 2) CUDA tensor of 8-byte elements")
+    aux_ptr, aux_n = (aux.data_ptr(), aux.numel() * aux.element_size()) if aux is not None else (None, 0)
+    st_ptr = None
+    if stats is not None:
+        if stats.numel() * stats.element_size() < STATS_BYTES:
+            raise ValueError("stats buffer too small")
+        st_ptr = stats.data_ptr()
+    rc = lib().pip_list_contract_ex(nodes.data_ptr(), nodes.shape[0], eps, _opt_ptr(make_options(**options)),
+                                    aux_ptr, aux_n, st_ptr, _stream_handle(stream))
+    _raise(rc, "pip_list_contract_ex")

@@ -157,6 +157,25 @@ bool cluster_supported(uint32_t elem_bytes, uint32_t cs, uint32_t threads, uint6
 pip_status launch_cluster_driver(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
                                  pip_stats* stats, cudaStream_t stream);
 
+// List contraction (list_driver.cu): plan and launch.
+struct ListPlan {
+  uint32_t n = 0;
+  uint32_t F = 0;        // fresh nodes per round
+  uint32_t kmax = 0;     // cap on active nodes per round
+  uint32_t kloc = 0;     // on-chip carried-node list per block
+  uint32_t blocks = 0;
+  uint32_t threads = 0;
+  uint32_t flags = 0;
+  uint64_t timeout_ns = 0;
+  uint64_t deadline_ns = 0;
+  uint64_t off_Q[2] = {0, 0};
+  uint64_t aux_bytes = 0;
+  uint64_t smem_bytes = 0;  // all blocks' on-chip lists (counted in the bound)
+  uint64_t aux_bound = 0;
+};
+pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out);
+pip_status launch_list_driver(const ListPlan& plan, void* rec, void* aux, pip_stats* stats, cudaStream_t stream);
+
 // Device facts cached per device.
 struct DeviceInfo {
   int sms = 0;
