@@ -123,6 +123,12 @@ typedef struct {
  * reservation per step.  Honoured by the grid and one-block drivers (the
  * planner does not choose the cluster driver under it). */
 #define PIP_FLAG_TWO_RES 512u
+/* pip_list_contract_ex: check the whole input (every pointer in range or NIL,
+ * prev and next consistent) before anything is modified, and reject it
+ * untouched with PIP_EINVAL.  Without it only the range of each pointer is
+ * checked, as the contraction reads it (an error then leaves the records
+ * unspecified); the full check costs two random reads per node. */
+#define PIP_FLAG_VALIDATE_INPUT 1024u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {
@@ -420,10 +426,13 @@ typedef struct {
  * after i in its original list (PIP_LIST_NIL where there is none) -- the tree
  * edges of the contraction.  The result equals splicing the nodes out one at
  * a time in index order.
- * Errors: an inconsistent input (pointer out of range, prev/next mismatch)
- * is found by a validation kernel before anything is modified and reported
- * as PIP_EINVAL by pip_check(); a cycle is detected when a round contracts
- * nothing and reported as PIP_EINTERNAL (the records are then unspecified).
+ * Errors (reported by pip_check()): a pointer out of range stops the run
+ * with PIP_EINVAL before any access outside the array; a cycle is detected
+ * when a round contracts nothing, PIP_EINTERNAL; in both cases the records
+ * are then unspecified.  Other inconsistent input (prev and next not
+ * matching) gives unspecified records.  With PIP_FLAG_VALIDATE_INPUT in
+ * pip_list_contract_ex the whole input is checked first and rejected
+ * untouched (PIP_EINVAL).
  * Scratch is allocated with cudaMallocAsync on `stream` and freed the same way.
  */
 pip_status pip_list_contract(pip_list_node *nodes_dev, uint64_t n, double eps, void *stream);

@@ -27,6 +27,13 @@
 // node (its R array) is needed: the marks live in a register bit mask of the
 // thread that owns the node for the round, and the only scratch is the loser
 // lists, on chip per block with an overflow queue in device memory.
+//
+// Input checks: phase A checks the range of both pointers of every record it
+// reads, and the first bad one stops the run at the next barrier with
+// PIP_EINVAL before phase B could follow it (every pointer a splice writes
+// was itself checked in that round), so no access leaves the array; the
+// records are then unspecified.  PIP_FLAG_VALIDATE_INPUT adds a full check of
+// the lists (range and prev / next consistency) before anything is modified.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -44,6 +51,9 @@ constexpr uint64_t kNil = PIP_LIST_NIL;
 constexpr unsigned kFullL = 0xffffffffu;
 constexpr uint32_t kMaxSlots = 32;  // items per thread and round (one mark bit each)
 constexpr uint32_t kListThreads = 512;
+#ifndef PIP_LIST_MIN_BLOCKS
+#define PIP_LIST_MIN_BLOCKS 2
+#endif
 
 struct ListArgs {
   ulonglong2* rec;
@@ -71,7 +81,7 @@ __device__ __forceinline__ void list_slice(uint32_t f, uint32_t* off, uint32_t* 
   *cnt = min(f, f0 + kf) - f0;
 }
 
-__global__ void __launch_bounds__(kListThreads, 2) list_rounds_kernel(const ListArgs a) {
+__global__ void __launch_bounds__(kListThreads, PIP_LIST_MIN_BLOCKS) list_rounds_kernel(const ListArgs a) {
   extern __shared__ uint32_t s_loc[];  // two on-chip lists of a.kloc carried nodes
   __shared__ uint32_t s_nloc[2];
   __shared__ uint32_t s_lcount, s_err;
@@ -151,6 +161,9 @@ __global__ void __launch_bounds__(kListThreads, 2) list_rounds_kernel(const List
       bool lm = false;
       if (act) {
         const ulonglong2 v = ld_rec(rec + i);
+        // a pointer out of range stops the run before phase B can use it;
+        // every pointer a splice writes comes from a record checked here
+        if ((v.x != kNil && v.x >= a.n) || (v.y != kNil && v.y >= a.n)) fail(PIP_EINVAL);
         lm = (v.x == kNil || v.x > i) && (v.y == kNil || v.y > i);
       }
       if (lm) marks |= 1u << q;
@@ -260,8 +273,11 @@ done:
   }
 }
 
-// Every pointer in range or NIL, and prev / next consistent; any violation
-// is recorded as PIP_EINVAL before the contraction kernel touches the lists.
+// Full input check (PIP_FLAG_VALIDATE_INPUT): every pointer in range or NIL,
+// and prev / next consistent; any violation is recorded as PIP_EINVAL before
+// the contraction kernel touches the lists.  It costs two random reads per
+// node, about half of a contraction, so it is opt-in; without it the
+// contraction kernel still checks the range of every pointer before using it.
 __global__ void validate_list_kernel(const ulonglong2* __restrict__ rec, uint32_t n, Ctrl* ctrl) {
   bool bad = false;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -330,9 +346,10 @@ pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPl
     if (per_sm > 0) want_b = std::min<uint64_t>(want_b, (uint64_t)per_sm * di.sms);
     p.blocks = (uint32_t)want_b;
     // every block handles at most kMaxSlots items per thread and round
-    // (fresh slice, on-chip list and overflow slice together; kmax <= 12 slots
-    // per thread keeps the sum within kMaxSlots)
-    const uint64_t cap = (uint64_t)p.blocks * threads * 12;
+    // (a block's items are at most kmax / blocks + kloc + 2: its fresh and
+    // overflow slices and its on-chip list; with kloc <= 8 slots of 512,
+    // kmax <= 20 slots per thread keeps the sum within kMaxSlots)
+    const uint64_t cap = (uint64_t)p.blocks * threads * 20;
     p.off_Q[0] = align256(sizeof(Ctrl));
     p.off_Q[1] = p.off_Q[0] + align256(4ull * p.kmax);
     p.aux_bytes = p.off_Q[1] + align256(4ull * p.kmax);
@@ -370,9 +387,11 @@ pip_status launch_list_driver(const ListPlan& plan, void* rec, void* aux, pip_st
   a.max_rounds = plan.n + 8u;
   a.flags = plan.flags;
   if (cudaMemsetAsync(aux, 0, plan.aux_bytes, stream) != cudaSuccess) return PIP_ECUDA;
-  const uint32_t vb = (uint32_t)std::min<uint64_t>(1024, (plan.n + 255) / 256);
-  validate_list_kernel<<<vb, 256, 0, stream>>>(a.rec, plan.n, a.ctrl);
-  if (cudaGetLastError() != cudaSuccess) return PIP_ECUDA;
+  if (plan.flags & PIP_FLAG_VALIDATE_INPUT) {
+    const uint32_t vb = (uint32_t)std::min<uint64_t>(1024, (plan.n + 255) / 256);
+    validate_list_kernel<<<vb, 256, 0, stream>>>(a.rec, plan.n, a.ctrl);
+    if (cudaGetLastError() != cudaSuccess) return PIP_ECUDA;
+  }
   DeviceInfo di;
   if (device_info(&di) != PIP_OK) return PIP_ECUDA;
   const int per_sm = list_blocks_per_sm(plan.threads, plan.kloc);

@@ -90,23 +90,45 @@ def test_launch_shapes(pip):
         assert np.array_equal(out, ref), opts
 
 
-def test_invalid_lists_are_rejected_untouched(pip):
+def test_invalid_lists_are_rejected_untouched_with_full_validation(pip):
     torch = torch_cuda()
     rec = workloads.random_lists(5000, rng_seed=3)
     bad = rec.copy()
     bad[17, 1] = 4999 if int(bad[17, 1]) != 4999 else 4998  # next no longer matches its prev
-    t = torch.from_numpy(bad.view(np.int64)).cuda()
-    pip.list_contract(t, eps=0.5)
+    oob = rec.copy()
+    oob[3, 0] = 10**9
+    for broken in (bad, oob):
+        t = torch.from_numpy(broken.view(np.int64)).cuda()
+        pip.list_contract(t, eps=0.5, flags=pip.FLAG_VALIDATE_INPUT)
+        with pytest.raises(pip.PipError) as e:
+            pip.check()
+        assert e.value.code == pip.PIP_EINVAL
+        assert np.array_equal(t.cpu().numpy().view(np.uint64), broken)
+    # valid input passes the full check
+    out, _ = gpu_contract(pip, rec, flags=pip.FLAG_VALIDATE_INPUT)
+    assert np.array_equal(out, expected(rec))
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_out_of_range_pointer_is_caught_in_flight(pip, which):
+    # Without the full check, the contraction itself checks every pointer's
+    # range before following it, and the call reports PIP_EINVAL.  The bad
+    # pointer is planted in a node whose neighbours are both larger, so no
+    # splice rewrites its record before the node is worked on.
+    torch = torch_cuda()
+    rec = workloads.random_lists(5000, rng_seed=4)
+    idx = np.arange(5000, dtype=np.uint64)
+    minima = np.nonzero(((rec[:, 0] == NIL) | (rec[:, 0] > idx)) & ((rec[:, 1] == NIL) | (rec[:, 1] > idx)))[0]
+    where = int(minima[[0, len(minima) // 2, -1][which]])
+    rec[where, 1] = 10**12
+    t = torch.from_numpy(rec.view(np.int64)).cuda()
+    pip.list_contract(t, eps=0.5, fresh_per_round=64)
     with pytest.raises(pip.PipError) as e:
         pip.check()
     assert e.value.code == pip.PIP_EINVAL
-    assert np.array_equal(t.cpu().numpy().view(np.uint64), bad)
-    oob = rec.copy()
-    oob[3, 0] = 10**9
-    t = torch.from_numpy(oob.view(np.int64)).cuda()
-    pip.list_contract(t, eps=0.5)
-    with pytest.raises(pip.PipError):
-        pip.check()
+    ok = workloads.random_lists(1000, rng_seed=1)
+    out, _ = gpu_contract(pip, ok)
+    assert np.array_equal(out, expected(ok))
 
 
 def test_cycle_is_reported(pip):
