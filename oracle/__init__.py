@@ -1,13 +1,14 @@
-"""CPU oracle for the parallel in-place random permutation and list contraction.
+"""CPU oracle for the parallel in-place random permutation, list contraction and scan.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  The product library never links, loads or calls it, and it shares no
 code with the CUDA path (see ``knuth.c`` for the arithmetic, written out from
 Section 4.1 of the paper and from the published SplitMix64 definition, and
-``listc.c`` for list contraction, Section 4.2).
+``listc.c`` for list contraction, Section 4.2, and ``scanc.c`` for the
+in-place scan, Section 5.1).
 
-The C part (``knuth.c``, ``listc.c``) is compiled with the host C compiler
+The C part (``knuth.c``, ``listc.c``, ``scanc.c``) is compiled with the host C compiler
 into ``_liboracle.so`` next to this file; :func:`build` does that and
 :func:`lib` loads it.
 """
@@ -21,7 +22,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "knuth.c"), os.path.join(_HERE, "listc.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("knuth.c", "listc.c", "scanc.c")]
 _SO = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -66,6 +67,10 @@ def lib() -> ctypes.CDLL:
             L.oracle_list_check.restype = ctypes.c_int
             L.oracle_list_nearest_larger.argtypes = [vp, u64, vp]
             L.oracle_list_nearest_larger.restype = ctypes.c_int
+            L.oracle_scan_u32.argtypes = [vp, u64, vp]
+            L.oracle_scan_u32.restype = None
+            L.oracle_scan_u64.argtypes = [vp, u64, vp]
+            L.oracle_scan_u64.restype = None
             _lib = L
     return _lib
 
@@ -173,3 +178,16 @@ def list_nearest_larger(rec: np.ndarray) -> np.ndarray:
     if lib().oracle_list_nearest_larger(rec.ctypes.data, rec.shape[0], out.ctypes.data) != 0:
         raise MemoryError("oracle_list_nearest_larger")
     return out
+
+
+# ------------------------------------------------------------------ scan
+def scan_exclusive(arr: np.ndarray) -> int:
+    """In-place exclusive scan of a 1-D uint32 or uint64 array by the
+    up-sweep / down-sweep of Algorithm 3 (Section 5.1), modulo 2^w; returns
+    the total."""
+    if arr.ndim != 1 or not arr.flags["C_CONTIGUOUS"] or arr.dtype not in (np.uint32, np.uint64):
+        raise ValueError("expected a contiguous 1-D uint32 or uint64 array")
+    tot = np.zeros(1, dtype=arr.dtype)
+    fn = lib().oracle_scan_u32 if arr.dtype == np.uint32 else lib().oracle_scan_u64
+    fn(arr.ctypes.data, arr.shape[0], tot.ctypes.data)
+    return int(tot[0])
