@@ -488,6 +488,57 @@ def run_list(args):
     return 0
 
 
+SCAN_BYTES_PER_ELEM = {"u32": 8, "u64": 16}  # each element read once and written once
+
+
+def run_scan(args):
+    """In-place exclusive scan (Section 5.1) of n unsigned integers (the
+    paper's scan input is 10^9 integers), values below 2^20 from a fixed
+    seed; each step scans the previous step's output (an equally valid
+    input).  Bound by HBM bandwidth: 2 x element bytes per element."""
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    n, dt = args.n, ("u32" if args.dtype == "u32" else "u64")
+    tdt = torch.int32 if dt == "u32" else torch.int64
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(args.seed)
+    A = torch.randint(0, 1 << 20, (n,), dtype=tdt, device="cuda", generator=gen)
+    tot = torch.zeros(1, dtype=tdt, device="cuda")
+    aux = torch.empty(pip.scan_aux_bytes(), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        pip.scan(A, total=tot, aux=aux)
+    pip.check()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s_, e_ in evs:
+            s_.record(stream)
+            pip.scan(A, total=tot, aux=aux)
+            e_.record(stream)
+        pip.check()
+    times = [s_.elapsed_time(e_) for s_, e_ in evs]
+    ms = sorted(times)[len(times) // 2]
+    ach = SCAN_BYTES_PER_ELEM[dt] * n / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    line = {
+        "metric": "scanned elems/s", "value": n / (ms / 1e3), "unit": "elems/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dt, "data": "synthetic",
+        "config": {"workload": f"inplace_exclusive_scan_n{n}_{dt}", "n": n, "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_elem": SCAN_BYTES_PER_ELEM[dt]},
+        "aux_bytes": pip.scan_aux_bytes(), "gpu_launches": args.steps, "clocks": clk.summary(), "step_ms": times,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _percentile(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -639,7 +690,7 @@ def main():
     ap.add_argument("--grid-blocks", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--flags", type=int, default=0, help="PIP_FLAG_* bits (2 = L2 prefetch of the next block)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "floor", "list"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "floor", "list", "scan"])
     ap.add_argument("--batch-count", type=int, default=8192)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--requests", type=int, default=1000)
@@ -660,6 +711,8 @@ def main():
         return run_serve(args)
     if args.workload == "floor":
         return run_floor(args)
+    if args.workload == "scan":
+        return run_scan(args)
     if args.workload == "list":
         if args.n == 10**9:
             args.n = 2 * 10**8  # the paper's largest list

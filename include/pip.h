@@ -451,6 +451,33 @@ pip_status pip_list_contract_ex(pip_list_node *nodes_dev, uint64_t n, double eps
  * aux_bytes, smem_bytes, aux_bound_bytes, min_rounds; driver = 3. */
 pip_status pip_list_plan(uint64_t n, double eps, const pip_options *opt, pip_plan_info *out);
 
+/* ------------------------------------------------------------ scan */
+
+/*
+ * pip_scan -- in-place exclusive prefix sum (Section 5.1, Algorithm 3): on
+ * return A[i] = A[0] + ... + A[i-1] (A[0] = 0) with the addition of w-bit
+ * unsigned integers modulo 2^w, and *total_dev (if not NULL) holds the sum of
+ * all n inputs.
+ *   A_dev    : device array of n elements, 16-byte aligned.
+ *   dtype    : PIP_U32 or PIP_U64.
+ *   total_dev: NULL or a device pointer to one element of dtype.
+ * The auxiliary device memory is a constant pip_scan_aux_bytes() (64 KB),
+ * whatever n (the space bound of the paper's strong PIP algorithm): a
+ * control block and a ring of tile descriptors.  Allocated with
+ * cudaMallocAsync on `stream` and freed the same way.  A bounded device-side
+ * wait that runs out is reported as PIP_ETIMEOUT by pip_check() (A is then
+ * unspecified).
+ */
+pip_status pip_scan(void *A_dev, uint64_t n, pip_dtype dtype, void *total_dev, void *stream);
+
+/* pip_scan_ex -- the same with caller-provided scratch (aux_dev: at least
+ * pip_scan_aux_bytes() device bytes, 256-byte aligned), or NULL to allocate. */
+pip_status pip_scan_ex(void *A_dev, uint64_t n, pip_dtype dtype, void *total_dev, void *aux_dev,
+                       uint64_t aux_bytes, void *stream);
+
+/* pip_scan_aux_bytes -- the fixed scratch size of pip_scan_ex. */
+uint64_t pip_scan_aux_bytes(void);
+
 /* pip_status_string -- static English description of a status code. */
 const char *pip_status_string(pip_status s);
 

@@ -255,6 +255,12 @@ def lib() -> ctypes.CDLL:
         L.pip_list_contract_ex.restype = i32
         L.pip_list_plan.argtypes = [u64, dbl, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
         L.pip_list_plan.restype = i32
+        L.pip_scan.argtypes = [vp, u64, i32, vp, vp]
+        L.pip_scan.restype = i32
+        L.pip_scan_ex.argtypes = [vp, u64, i32, vp, vp, u64, vp]
+        L.pip_scan_ex.restype = i32
+        L.pip_scan_aux_bytes.argtypes = []
+        L.pip_scan_aux_bytes.restype = u64
         _lib = L
         return L
 
@@ -579,3 +585,25 @@ def list_contract(nodes, eps: float = 0.5, *, stream=None, aux=None, stats=None,
     rc = lib().pip_list_contract_ex(nodes.data_ptr(), nodes.shape[0], eps, _opt_ptr(make_options(**options)),
                                     aux_ptr, aux_n, st_ptr, _stream_handle(stream))
     _raise(rc, "pip_list_contract_ex")
+
+
+# ------------------------------------------------------------------ scan
+def scan(A, total=None, *, stream=None, aux=None) -> None:
+    """In-place exclusive prefix sum of the 1-D CUDA tensor ``A`` (4- or 8-byte
+    elements, added as unsigned integers modulo 2^w); ``total``: optional CUDA
+    tensor of at least one element of A's size that receives the sum."""
+    if not A.is_cuda or not A.is_contiguous() or A.dim() != 1 or A.element_size() not in (4, 8):
+        raise ValueError("A must be a contiguous 1-D CUDA tensor of 4- or 8-byte elements")
+    d = U32 if A.element_size() == 4 else U64
+    t_ptr = None
+    if total is not None:
+        if not total.is_cuda or total.element_size() != A.element_size() or total.numel() < 1:
+            raise ValueError("total must be a CUDA tensor of A's element size")
+        t_ptr = total.data_ptr()
+    aux_ptr, aux_n = (aux.data_ptr(), aux.numel() * aux.element_size()) if aux is not None else (None, 0)
+    _raise(lib().pip_scan_ex(A.data_ptr(), A.shape[0], d, t_ptr, aux_ptr, aux_n, _stream_handle(stream)),
+           "pip_scan_ex")
+
+
+def scan_aux_bytes() -> int:
+    return int(lib().pip_scan_aux_bytes())

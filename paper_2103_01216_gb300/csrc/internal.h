@@ -176,6 +176,9 @@ struct ListPlan {
 pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out);
 pip_status launch_list_driver(const ListPlan& plan, void* rec, void* aux, pip_stats* stats, cudaStream_t stream);
 
+// Scan (scan.cu): bytes of the fixed scratch (control block and descriptor ring).
+uint64_t scan_aux_bytes();
+
 // Device facts cached per device.
 struct DeviceInfo {
   int sms = 0;
