@@ -1,14 +1,14 @@
-"""CPU oracle for the parallel in-place random permutation, list contraction and scan.
+"""CPU oracle for the parallel in-place random permutation, list and tree contraction and scan.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  The product library never links, loads or calls it, and it shares no
 code with the CUDA path (see ``knuth.c`` for the arithmetic, written out from
 Section 4.1 of the paper and from the published SplitMix64 definition, and
-``listc.c`` for list contraction, Section 4.2, and ``scanc.c`` for the
-in-place scan, Section 5.1).
+``listc.c`` for list contraction and ``treec.c`` for tree contraction,
+Section 4.2, and ``scanc.c`` for the in-place scan, Section 5.1).
 
-The C part (``knuth.c``, ``listc.c``, ``scanc.c``) is compiled with the host C compiler
+The C part (``knuth.c``, ``listc.c``, ``treec.c``, ``scanc.c``) is compiled with the host C compiler
 into ``_liboracle.so`` next to this file; :func:`build` does that and
 :func:`lib` loads it.
 """
@@ -22,7 +22,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, f) for f in ("knuth.c", "listc.c", "scanc.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("knuth.c", "listc.c", "treec.c", "scanc.c")]
 _SO = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -67,6 +67,14 @@ def lib() -> ctypes.CDLL:
             L.oracle_list_check.restype = ctypes.c_int
             L.oracle_list_nearest_larger.argtypes = [vp, u64, vp]
             L.oracle_list_nearest_larger.restype = ctypes.c_int
+            L.oracle_tree_contract.argtypes = [vp, u64, u64, u64]
+            L.oracle_tree_contract.restype = ctypes.c_int64
+            L.oracle_tree_contract_seq.argtypes = [vp, u64]
+            L.oracle_tree_contract_seq.restype = ctypes.c_int
+            L.oracle_tree_check.argtypes = [vp, u64]
+            L.oracle_tree_check.restype = ctypes.c_int
+            L.oracle_tree_uncontract.argtypes = [vp, u64, vp, u64, vp]
+            L.oracle_tree_uncontract.restype = ctypes.c_int
             L.oracle_scan_u32.argtypes = [vp, u64, vp]
             L.oracle_scan_u32.restype = None
             L.oracle_scan_u64.argtypes = [vp, u64, vp]
@@ -178,6 +186,56 @@ def list_nearest_larger(rec: np.ndarray) -> np.ndarray:
     if lib().oracle_list_nearest_larger(rec.ctypes.data, rec.shape[0], out.ctypes.data) != 0:
         raise MemoryError("oracle_list_nearest_larger")
     return out
+
+
+# ------------------------------------------------------------------ tree contraction
+def _tree_records(rec) -> np.ndarray:
+    rec = np.asarray(rec)
+    if rec.dtype != np.uint64 or rec.ndim != 2 or rec.shape[1] != 4 or not rec.flags["C_CONTIGUOUS"]:
+        raise ValueError("records must be a C-contiguous (n, 4) uint64 array of (parent, left, right, round)")
+    return rec
+
+
+def tree_contract(rec: np.ndarray, F: int, kmax: int) -> int:
+    """Contract the forest in ``rec`` in place by the round schedule with fresh
+    block ``F`` and active-set cap ``kmax`` (Section 4.2); returns the rounds."""
+    rec = _tree_records(rec)
+    r = int(lib().oracle_tree_contract(rec.ctypes.data, rec.shape[0], F, kmax))
+    if r == -2:
+        raise MemoryError("oracle_tree_contract")
+    if r < 0:
+        raise ValueError(f"inconsistent tree input ({r})")
+    return r
+
+
+def tree_contract_seq(rec: np.ndarray) -> np.ndarray:
+    """Rake every leaf in increasing index order (leaf i in round i + 1)."""
+    rec = _tree_records(rec)
+    if lib().oracle_tree_contract_seq(rec.ctypes.data, rec.shape[0]) != 0:
+        raise ValueError("inconsistent tree input")
+    return rec
+
+
+def tree_check(rec: np.ndarray) -> int:
+    """0 when ``rec`` holds a valid forest of full binary trees, else a negative code."""
+    rec = _tree_records(rec)
+    return int(lib().oracle_tree_check(rec.ctypes.data, rec.shape[0]))
+
+
+def tree_uncontract(out: np.ndarray, orig: np.ndarray) -> tuple[int, np.ndarray]:
+    """Undo the rakes recorded in ``out`` (a copy is modified) in decreasing
+    round order; returns (status, records), status 0 when every step was
+    consistent.  ``orig`` is the input the contraction started from: its
+    leaves whose left word is no longer NIL are the raked ones (a raked leaf
+    records its sibling there), and its round words are put back."""
+    rec = np.ascontiguousarray(_tree_records(out).copy())
+    orig = _tree_records(orig)
+    n = rec.shape[0]
+    raked = np.nonzero((orig[:, 1] == NIL) & (rec[:, 1] != NIL))[0].astype(np.uint64)
+    raked = np.ascontiguousarray(raked)
+    orr = np.ascontiguousarray(orig[:, 3])
+    rc = int(lib().oracle_tree_uncontract(rec.ctypes.data, n, raked.ctypes.data, raked.shape[0], orr.ctypes.data))
+    return rc, rec
 
 
 # ------------------------------------------------------------------ scan

@@ -1,5 +1,5 @@
 """Round-by-round simulators of the parallel Knuth shuffle and of parallel
-list contraction (debugging aids).
+list and tree contraction (debugging aids and cross-checks).
 
 TEST INFRASTRUCTURE ONLY (same rule as the rest of ``oracle/``).
 
@@ -117,4 +117,64 @@ def list_rounds(rec, k: int | None = None):
         done = set(marked)
         todo = [i for i in todo if i not in done]
         rounds.append(done)
+    return rec, rounds
+
+
+def tree_rounds(rec, F: int, kmax: int):
+    """Tree contraction under the prefix schedule (Section 4.2), written
+    independently of ``treec.c`` as a cross-check on small forests.
+
+    rec: list of [parent, left, right, round] over nodes 0..n-1, None for a
+    missing pointer.  Round r (from 1) works on the carried leaves plus the
+    next fn = min(F, unadmitted, kmax - m + 1) node ids (m the previous
+    active count; fn = min(F, n) in round 1).  An active leaf with a parent
+    is raked when no leaf among its sibling, its nephews (children of the
+    sibling) and its uncle (the other child of the grandparent) has a smaller
+    id, else carried (both decided on the state at the start of the round,
+    so a carried leaf may have become a root meanwhile).  Raking x with
+    parent p, sibling s, grandparent g splices p out (s takes its place) and
+    sets x's record to [p, s, g, r].  Returns (records, per-round raked sets).
+    """
+    rec = [list(r) for r in rec]
+    n = len(rec)
+
+    def leaf(v):
+        return rec[v][1] is None and rec[v][2] is None
+
+    def kids(v):
+        return [rec[v][1], rec[v][2]]
+
+    admitted, carried, m_prev, rounds = 0, [], 0, []
+    while True:
+        fn = min(F, n - admitted)
+        if rounds:
+            fn = min(fn, kmax - m_prev + 1)
+        active = carried + list(range(admitted, admitted + fn))
+        admitted += fn
+        if not active:
+            break
+        r = len(rounds) + 1
+        plan, carried = {}, []
+        for x in active:
+            if not leaf(x) or rec[x][0] is None:
+                continue
+            p = rec[x][0]
+            s = [c for c in kids(p) if c != x][0]
+            g = rec[p][0]
+            rivals = [s] if leaf(s) else kids(s)
+            if g is not None:
+                rivals += [c for c in kids(g) if c != p]
+            if all(not leaf(y) or y > x for y in rivals):
+                plan[x] = (p, s, g)
+            else:
+                carried.append(x)
+        for x, (p, s, g) in plan.items():
+            rec[s][0] = g
+            if g is not None:
+                rec[g][1 if rec[g][1] == p else 2] = s
+            rec[x] = [p, s, g, r]
+        if carried and not plan:
+            raise RuntimeError("no leaf raked in a round")
+        rounds.append(set(plan))
+        m_prev = len(active)
     return rec, rounds

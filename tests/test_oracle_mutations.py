@@ -193,3 +193,93 @@ def test_planted_list_mistake_is_caught(name, tmp_path):
     assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
     L = _compile_list(text.replace(old, new), str(tmp_path / f"{name}.so"))
     assert not _list_pins_pass(L), f"pins did not catch mutation {name}"
+
+
+# ---------------------------------------------------------------- tree contraction
+TREE_SRC = os.path.join(ROOT, "oracle", "treec.c")
+
+TREE_MUTATIONS = {
+    "record_swaps_sibling_and_grandparent": ("LEFT(x) = s;\n    RIGHT(x) = g;", "LEFT(x) = g;\n    RIGHT(x) = s;"),
+    "sibling_keeps_old_parent": ("    PAR(s) = g;\n    if (g != T_NIL) {\n        if (LEFT(g) == p) LEFT(g) = s;",
+                                 "    if (g != T_NIL) {\n        if (LEFT(g) == p) LEFT(g) = s;"),
+    "grandparent_slot_not_updated": ("        if (LEFT(g) == p) LEFT(g) = s;\n        else RIGHT(g) = s;", ""),
+    "drops_uncle_check": ("if (is_leaf(rec, u) && u < x) return 0;        /* uncle */", ""),
+    "drops_a_nephew_check": ("if (is_leaf(rec, b) && b < x) return 0;", ""),
+    "drops_sibling_check": ("if (s < x) return 0;                          /* sibling */", ""),
+    "round_off_by_one": ("ROUND(x) = r;", "ROUND(x) = r + 1;"),
+    "ignores_the_throttle": ("if (rounds > 0 && kmax - m_prev + 1 < fn) fn = kmax - m_prev + 1;", ""),
+    "rakes_while_deciding": ("rakes[j] = ok ? 1 : 2;", "rakes[j] = ok ? 3 : 2;\n            if (ok) rake(rec, x, rounds);"),
+    "larger_index_wins": ("if (s < x) return 0;                          /* sibling */",
+                          "if (s > x) return 0;                          /* sibling */"),
+}
+
+
+def _compile_tree(src_text, path):
+    c = path + ".c"
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", path, c])
+    L = ctypes.CDLL(path)
+    L.oracle_tree_contract.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+    L.oracle_tree_contract.restype = ctypes.c_int64
+    return L
+
+
+def _tree_pins_pass(L):
+    """The tree pins of test_oracle_tree.py in compact form: one node per
+    round against a Python sequential rake, larger prefixes against the
+    Python round simulator, and every output undone by the real oracle's
+    uncontract back to the input."""
+    import oracle
+    import workloads
+    from oracle.rounds import tree_rounds
+
+    nil = int(oracle.NIL)
+
+    def tolist(a):
+        return [[None if int(v) == nil else int(v) for v in row] for row in a]
+
+    def seq(rows):
+        rec = [list(r) for r in rows]
+        for x in range(len(rec)):
+            if rec[x][1] is not None or rec[x][0] is None:
+                continue
+            p = rec[x][0]
+            s = rec[p][2] if rec[p][1] == x else rec[p][1]
+            g = rec[p][0]
+            rec[s][0] = g
+            if g is not None:
+                rec[g][1 if rec[g][1] == p else 2] = s
+            rec[x] = [p, s, g, x + 1]
+        return rec
+
+    for seed in range(12):
+        inp = workloads.random_tree(3 + 7 * seed, 900 + seed, trees=1 + seed % 3)
+        for F, k in ((1, 4), (3, 9), (5, 7), (10**6, 10**6)):
+            out = inp.copy()
+            if L.oracle_tree_contract(out.ctypes.data, out.shape[0], F, k) < 0:
+                return False
+            if F == 1 and tolist(out) != seq(tolist(inp)):
+                return False
+            if F > 1 and tolist(out) != tree_rounds(tolist(inp), F, k)[0]:
+                return False
+            rc, back = oracle.tree_uncontract(out, inp)
+            if rc != 0 or not np.array_equal(back, inp):
+                return False
+    return True
+
+
+def test_real_tree_oracle_passes_compact_pins(tmp_path):
+    with open(TREE_SRC) as f:
+        L = _compile_tree(f.read(), str(tmp_path / "real_tree.so"))
+    assert _tree_pins_pass(L)
+
+
+@pytest.mark.parametrize("name", sorted(TREE_MUTATIONS))
+def test_planted_tree_mistake_is_caught(name, tmp_path):
+    old, new = TREE_MUTATIONS[name]
+    with open(TREE_SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    L = _compile_tree(text.replace(old, new), str(tmp_path / f"{name}.so"))
+    assert not _tree_pins_pass(L), f"pins did not catch mutation {name}"

@@ -10,7 +10,10 @@ The paper measures on synthetic arrays of 10 million to 1 billion 64-bit
 integers (Section 7.2); the shapes below follow that: A[i] = i keys of 4 or 8
 bytes, and 16-byte records {key = i, payload = mix(i)}.  For list contraction
 it uses 10 to 200 million nodes of two 64-bit pointers (Section 7.3): random
-doubly-linked lists over node ids 0..n-1, NIL = 2^64 - 1 at the ends.
+doubly-linked lists over node ids 0..n-1, NIL = 2^64 - 1 at the ends.  For
+tree contraction (same section, same sizes) it uses forests of rooted binary
+trees in which every internal node has two children, one 32-byte record
+(parent, left, right, round) per node, with node ids in random order.
 """
 from __future__ import annotations
 
@@ -133,3 +136,94 @@ def random_lists(n: int, rng_seed: int, nlists: int = 1) -> np.ndarray:
     uniform permutation from numpy's PCG64 seeded with ``rng_seed``."""
     order = np.random.default_rng(rng_seed).permutation(n).astype(np.uint64)
     return lists_from_order(order, nlists)
+
+
+TREE_NIL = LIST_NIL
+
+
+def tree_records(parent: np.ndarray, left: np.ndarray, right: np.ndarray, perm: np.ndarray | None = None,
+                 round_fill: int = 0) -> np.ndarray:
+    """(n, 4) uint64 records (parent, left, right, round) of a forest given by
+    parent / child arrays over ids 0..n-1 (NIL = 2^64 - 1), with every id x
+    renamed perm[x] when ``perm`` is given; the round words hold ``round_fill``."""
+    parent = np.asarray(parent, dtype=np.uint64)
+    left = np.asarray(left, dtype=np.uint64)
+    right = np.asarray(right, dtype=np.uint64)
+    n = parent.shape[0]
+    rec = np.full((n, 4), TREE_NIL, dtype=np.uint64)
+    rec[:, 3] = np.uint64(round_fill)
+    if n == 0:
+        return rec
+    if perm is None:
+        perm = np.arange(n, dtype=np.uint64)
+    perm = np.asarray(perm, dtype=np.uint64)
+
+    def ren(a):
+        out = np.full(n, TREE_NIL, dtype=np.uint64)
+        ok = a != TREE_NIL
+        out[ok] = perm[a[ok].astype(np.int64)]
+        return out
+
+    idx = perm.astype(np.int64)
+    rec[idx, 0] = ren(parent)
+    rec[idx, 1] = ren(left)
+    rec[idx, 2] = ren(right)
+    return rec
+
+
+def random_tree(leaves: int, rng_seed: int, trees: int = 1, round_fill: int = 0) -> np.ndarray:
+    """A forest of ``trees`` random binary trees with ``leaves`` leaves in all
+    (every internal node has two children; 2 * leaves - trees nodes).  Each
+    tree is built bottom-up: its current roots are shuffled and joined in
+    pairs under new internal nodes, level after level, which gives trees of
+    depth about log2 of their leaves; then all node ids are renamed by a
+    uniform permutation, so that priorities (ids) carry no information about
+    the shape.  numpy's PCG64 seeded with ``rng_seed`` drives both steps."""
+    rng = np.random.default_rng(rng_seed)
+    trees = max(1, min(trees, leaves))
+    n = 2 * leaves - trees
+    parent = np.full(n, TREE_NIL, dtype=np.uint64)
+    left = np.full(n, TREE_NIL, dtype=np.uint64)
+    right = np.full(n, TREE_NIL, dtype=np.uint64)
+    cuts = np.linspace(0, leaves, trees + 1).astype(np.int64)
+    nxt = leaves
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        roots = np.arange(a, b, dtype=np.int64)
+        while roots.shape[0] > 1:
+            roots = roots[rng.permutation(roots.shape[0])]
+            k = roots.shape[0] // 2
+            x, y = roots[:k], roots[k:2 * k]
+            new = np.arange(nxt, nxt + k, dtype=np.int64)
+            nxt += k
+            left[new] = x.astype(np.uint64)
+            right[new] = y.astype(np.uint64)
+            parent[x] = new.astype(np.uint64)
+            parent[y] = new.astype(np.uint64)
+            roots = np.concatenate([new, roots[2 * k:]])
+    assert nxt == n
+    perm = rng.permutation(n).astype(np.uint64)
+    return tree_records(parent, left, right, perm, round_fill)
+
+
+def caterpillar_tree(leaves: int, order: np.ndarray | None = None, round_fill: int = 0) -> np.ndarray:
+    """A caterpillar: internal nodes form one path (the spine) and each holds
+    one leaf, the deepest holding two.  Ids: leaves 0..leaves-1 from the
+    bottom of the spine up (renamed through ``order`` when given), internal
+    nodes after them from the bottom up."""
+    n = 2 * leaves - 1
+    parent = np.full(n, TREE_NIL, dtype=np.uint64)
+    left = np.full(n, TREE_NIL, dtype=np.uint64)
+    right = np.full(n, TREE_NIL, dtype=np.uint64)
+    if leaves > 1:
+        below = 0  # the subtree under the next spine node
+        for j in range(leaves - 1):
+            v = leaves + j
+            left[v] = np.uint64(below)
+            right[v] = np.uint64(j + 1)
+            parent[below] = np.uint64(v)
+            parent[j + 1] = np.uint64(v)
+            below = v
+    perm = np.arange(n, dtype=np.uint64)
+    if order is not None:
+        perm[:leaves] = np.asarray(order, dtype=np.uint64)
+    return tree_records(parent, left, right, perm, round_fill)
