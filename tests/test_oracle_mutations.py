@@ -10,6 +10,7 @@ import itertools
 import math
 import os
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -214,11 +215,15 @@ TREE_MUTATIONS = {
 }
 
 
-def _compile_tree(src_text, path):
+def _compile_tree(src_text, path, load=True):
     c = path + ".c"
     with open(c, "w") as f:
         f.write(src_text)
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", path, c])
+    return _load_tree(path) if load else None
+
+
+def _load_tree(path):
     L = ctypes.CDLL(path)
     L.oracle_tree_contract.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
     L.oracle_tree_contract.restype = ctypes.c_int64
@@ -275,11 +280,23 @@ def test_real_tree_oracle_passes_compact_pins(tmp_path):
     assert _tree_pins_pass(L)
 
 
+def _tree_pins_in_child(so_path):
+    """Runs the compact pins on a compiled mutant in a child process: a
+    mutant that corrupts the tree may crash, which also counts as caught.
+    Returns True when the pins all hold."""
+    code = ("import sys, ctypes; sys.path.insert(0, {root!r}); "
+            "from tests.test_oracle_mutations import _load_tree, _tree_pins_pass; "
+            "sys.exit(0 if _tree_pins_pass(_load_tree({so!r})) else 1)").format(root=ROOT, so=so_path)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, timeout=300)
+    return r.returncode == 0
+
+
 @pytest.mark.parametrize("name", sorted(TREE_MUTATIONS))
 def test_planted_tree_mistake_is_caught(name, tmp_path):
     old, new = TREE_MUTATIONS[name]
     with open(TREE_SRC) as f:
         text = f.read()
     assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
-    L = _compile_tree(text.replace(old, new), str(tmp_path / f"{name}.so"))
-    assert not _tree_pins_pass(L), f"pins did not catch mutation {name}"
+    so = str(tmp_path / f"{name}.so")
+    _compile_tree(text.replace(old, new), so, load=False)
+    assert not _tree_pins_in_child(so), f"pins did not catch mutation {name}"
