@@ -2,24 +2,34 @@
 // In-Place-Scan, exclusive prefix sums and the total, computed in place with
 // only a bounded amount of auxiliary space).
 //
-// The GPU design is a single pass over the array in tiles of 96 KB with
-// decoupled look-back: block b of a grid of G resident blocks takes tiles
-// b, b + G, ..., moves each into shared memory with a bulk asynchronous copy
-// (cp.async.bulk, completion on an mbarrier; the next tile's copy is in
-// flight while the current one is scanned), scans it there, publishes the
-// tile's sum in a descriptor, derives the sum of everything before the tile
-// from its predecessors' descriptors (the look-back, 32 descriptors per
-// round trip), publishes the inclusive prefix, adds the prefix and writes
-// the tile back with a bulk copy from shared memory.  Each element is read
-// once and written once: the pass is bound by HBM bandwidth.
+// The GPU design is a single pass over the array in tiles with decoupled
+// look-back: block b of a grid of G resident blocks takes tiles b, b + G,
+// ..., each moved into shared memory by a bulk asynchronous copy
+// (cp.async.bulk completing on an mbarrier) into a ring of kStages tile
+// buffers, kStages - 2 copies ahead of the tile being scanned.  The block is
+// warp-specialised:
+//   - the scanning warps scan tile i in shared memory (each thread a run of
+//     consecutive elements, then the warps), publish the tile's sum in a
+//     descriptor, hand it to the look-back warp and, one tile behind, add
+//     the prefix the look-back warp found for tile i - 1 and send that tile
+//     back with a bulk copy from shared memory;
+//   - the look-back warp derives the sum of everything before tile i from
+//     its predecessors' descriptors (the look-back, 32 * kLbPerLane
+//     descriptors per L2 round trip) and publishes the inclusive prefix,
+//     while the scanning warps work on the next tile.
+// So the look-back's latency overlaps the data path instead of stalling it,
+// and each element is read once and written once: the pass is bound by HBM
+// bandwidth.
 //
 // The descriptors form a ring of kRing entries reused modulo kRing, tagged
-// with the tile index; at most two tiles per resident block are in flight
-// (one being scanned, the next one loading) and a look-back reaches back at
-// most that far, so a ring of more than four times the resident blocks is
-// never overwritten while it is read.  The auxiliary
-// space is therefore a constant (the ring and a control block, about 32 KB),
-// whatever n -- the space bound of the paper's strong PIP algorithm.
+// with the tile index.  A block publishes the sum of a tile only after the
+// look-back of its tile two places earlier has ended, and a look-back never
+// reads further back than the tile G places earlier (whose prefix its block
+// published before it started), so the tiles whose descriptors are read or
+// written at one time span fewer than 6 G indices; a ring of 8 G or more is
+// never overwritten while it is read.  The auxiliary space is therefore a
+// constant (the ring and a control block, 64 KB), whatever n -- the space
+// bound of the paper's strong PIP algorithm.
 //
 // Addition is modulo 2^w (w = 32 or 64), which is associative, so the result
 // does not depend on the order in which partial sums are combined: the
@@ -35,21 +45,31 @@
 namespace pip {
 namespace {
 
-// Tile size and block size: 96 KB tiles (two per block, one block per SM)
-// and 1024 threads measured best on GB300 (57 % of the HBM copy bandwidth at
-// 10^9 elements, against 44-56 % for 32-64 KB tiles): a tile's look-back
-// costs a few L2 round trips whatever its size, so larger tiles spend less
-// of the pass waiting for it.
+// Shape: kStages tile buffers of PIP_SCAN_TILE_KB each (one block per SM),
+// PIP_SCAN_THREADS scanning threads plus the look-back warp.
 #ifndef PIP_SCAN_THREADS
-#define PIP_SCAN_THREADS 1024
+#define PIP_SCAN_THREADS 512
 #endif
 #ifndef PIP_SCAN_TILE_KB
-#define PIP_SCAN_TILE_KB 96
+#define PIP_SCAN_TILE_KB 48
 #endif
-constexpr uint32_t kScanThreads = PIP_SCAN_THREADS;
-constexpr uint32_t kTileBytes = PIP_SCAN_TILE_KB * 1024;  // per block and tile
-constexpr uint32_t kRing = 4096;        // descriptors, a power of two
+#ifndef PIP_SCAN_STAGES
+#define PIP_SCAN_STAGES 4
+#endif
+#ifndef PIP_SCAN_LB_PER_LANE
+#define PIP_SCAN_LB_PER_LANE 1
+#endif
+constexpr uint32_t kScanThreads = PIP_SCAN_THREADS;     // scanning threads
+constexpr uint32_t kBlockThreads = kScanThreads + 32u;  // and the look-back warp
+constexpr uint32_t kStages = PIP_SCAN_STAGES;           // tile buffers
+constexpr uint32_t kAhead = kStages - 2u;               // copies in flight ahead
+constexpr uint32_t kTileBytes = PIP_SCAN_TILE_KB * 1024;
+constexpr uint32_t kSmemBytes = kStages * kTileBytes;  // dynamic shared memory
+constexpr uint32_t kLbPerLane = PIP_SCAN_LB_PER_LANE;
+constexpr uint32_t kRing = 4096;  // descriptors, a power of two
 constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
+constexpr uint32_t kBarScan = 1, kBarHandoff = 2;  // named barriers
+static_assert(kStages >= 3 && kScanThreads % 32u == 0 && kBlockThreads <= 1024u, "scan shape");
 
 struct ScanCtrl {
   unsigned long long unused;
@@ -77,19 +97,27 @@ __device__ __forceinline__ unsigned long long desc_word(uint64_t tile, uint64_t 
   return ((tile & kTagMask) << 40) | (flag << 38) | (unsigned long long)half;
 }
 
+// Descriptor words are written and read with relaxed gpu-scope accesses: a
+// tile's sum and its prefix are written by two threads of one block ordered
+// by a barrier, and such strong accesses keep that order in every reader's
+// view of the word.
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ void desc_publish(ScanDesc* d, uint64_t tile, uint64_t flag, T value) {
   const unsigned long long v = (unsigned long long)value;
-  __stcg(&d->w[1], desc_word(tile, flag, (uint32_t)(v >> 32)));
-  __stcg(&d->w[0], desc_word(tile, flag, (uint32_t)v));
+  st_relaxed_u64(&d->w[1], desc_word(tile, flag, (uint32_t)(v >> 32)));
+  st_relaxed_u64(&d->w[0], desc_word(tile, flag, (uint32_t)v));
 }
 
 // 0 when the descriptor does not (yet) describe `tile`; else its flag, with
 // the value in *value.
 template <typename T>
 __device__ __forceinline__ uint64_t desc_read(const ScanDesc* d, uint64_t tile, T* value) {
-  const unsigned long long a = __ldcg(&d->w[0]);
-  const unsigned long long b = __ldcg(&d->w[1]);
+  const unsigned long long a = ld_relaxed_u64(&d->w[0]);
+  const unsigned long long b = ld_relaxed_u64(&d->w[1]);
   const uint64_t tag = tile & kTagMask;
   if ((a >> 40) != tag || (b >> 40) != tag) return 0;
   const uint64_t fa = (a >> 38) & 3ull, fb = (b >> 38) & 3ull;
@@ -156,9 +184,15 @@ __device__ __forceinline__ T warp_incl_scan(T v, uint32_t lane) {
   return v;
 }
 
-// Warp 0's part of a tile: the decoupled look-back.  Lane k reads the
-// descriptor of tile t-1-k, 32 predecessors per round trip, and the warp
-// adds the aggregates back to the nearest published inclusive prefix.
+// The look-back warp's part of a tile: the decoupled look-back.  Lane k reads
+// the descriptors of tiles top-kQ-q (q < kLbPerLane), 32 * kLbPerLane
+// predecessors per window (their loads are independent, so a window costs
+// one L2 latency), and the warp adds them from the top down to the nearest
+// published inclusive prefix.  A window that is ready only in part still
+// counts: its ready run from the top is added, and then lane 0 alone polls
+// the first descriptor that was not ready (with a short sleep between
+// polls, so that spinning warps do not crowd the L2 lines their
+// predecessors are publishing to) before the next window starts there.
 // Returns the exclusive prefix of tile t (in every lane), or sets *fail.
 template <typename T>
 __device__ __forceinline__ T look_back(const ScanDesc* ring, uint64_t t, uint32_t lane, ScanCtrl* ctrl,
@@ -166,154 +200,239 @@ __device__ __forceinline__ T look_back(const ScanDesc* ring, uint64_t t, uint32_
   T prefix = 0;
   int64_t top = (int64_t)t - 1;  // highest predecessor not yet accounted for
   uint64_t t0 = 0;
-  uint32_t polls = 0;
   while (top >= 0) {
-    const int64_t j = top - (int64_t)lane;
-    uint64_t flag = 1;  // lanes beyond tile 0 count as ready aggregates of 0
-    T val = 0;
-    if (j >= 0) flag = desc_read<T>(ring + (j & (kRing - 1)), (uint64_t)j, &val);
-    // the window is usable up to (and including) the nearest inclusive
-    // prefix; every descriptor before it must be ready
-    const unsigned pmask = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
-    const uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 31u;
-    const unsigned rmask = __ballot_sync(0xffffffffu, flag != 0);
-    const unsigned need = stop == 31u ? 0xffffffffu : ((1u << (stop + 1u)) - 1u);
-    if ((rmask & need) == need) {
-      T v = lane <= stop ? val : T(0);
+    uint64_t flag[kLbPerLane];
+    T val[kLbPerLane];
 #pragma unroll
-      for (uint32_t d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-      prefix += v;
-      if (pmask || top < 32) break;  // reached a prefix, or tile 0
-      top -= 32;
-      continue;
+    for (uint32_t q = 0; q < kLbPerLane; ++q) {
+      const int64_t j = top - (int64_t)(lane * kLbPerLane + q);
+      flag[q] = kFlagAgg;  // below tile 0: ready aggregates of 0
+      val[q] = 0;
+      if (j >= 0) flag[q] = desc_read<T>(ring + (j & (kRing - 1)), (uint64_t)j, &val[q]);
     }
-    if ((++polls & 63u) == 0u) {
-      uint32_t bad = 0;
-      if (lane == 0) {
-        if (ld_relaxed_u32(&ctrl->status) != 0u) bad = 1;
-        const uint64_t now = globaltimer_ns();
-        if (t0 == 0) t0 = now;
-        else if (now - t0 > timeout_ns) {
-          set_status(&ctrl->status, PIP_ETIMEOUT);
-          bad = 1;
+    // this lane's ready run from its top: cnt descriptors, ending at a
+    // prefix when found
+    uint32_t cnt = kLbPerLane;
+    bool found = false;
+#pragma unroll
+    for (int q = (int)kLbPerLane - 1; q >= 0; --q) {
+      if (flag[q] == 0) {
+        cnt = (uint32_t)q;
+        found = false;
+      } else if (flag[q] == kFlagPrefix) {
+        cnt = (uint32_t)q + 1u;
+        found = true;
+      }
+    }
+    // the first lane that stops the run (a gap or a prefix) bounds the
+    // window: lanes before it contribute everything, it contributes cnt
+    const unsigned full = __ballot_sync(0xffffffffu, cnt == kLbPerLane && !found);
+    const uint32_t last = full == 0xffffffffu ? 32u : (uint32_t)(__ffs(~full) - 1);
+    const uint32_t last_cnt = last < 32u ? __shfl_sync(0xffffffffu, cnt, last) : 0u;
+    const bool done = last < 32u && __shfl_sync(0xffffffffu, (uint32_t)found, last) != 0u;
+    T v = 0;
+    const uint32_t take = lane < last ? kLbPerLane : (lane == last ? last_cnt : 0u);
+#pragma unroll
+    for (uint32_t q = 0; q < kLbPerLane; ++q)
+      if (q < take) v += val[q];
+#pragma unroll
+    for (uint32_t d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    prefix += v;
+    if (done) break;
+    top -= (int64_t)(last * kLbPerLane + last_cnt);
+    if (last == 32u || top < 0) continue;  // the whole window was ready
+    // lane 0 waits for descriptor `top` (bounded), then the warp goes on
+    uint32_t bad = 0;
+    if (lane == 0) {
+      T unused;
+      for (uint32_t k = 0; desc_read<T>(ring + (top & (kRing - 1)), (uint64_t)top, &unused) == 0; ++k) {
+        __nanosleep(64);
+        if ((k & 15u) == 15u) {
+          if (ld_relaxed_u32(&ctrl->status) != 0u) {
+            bad = 1;
+            break;
+          }
+          const uint64_t now = globaltimer_ns();
+          if (t0 == 0) t0 = now;
+          else if (now - t0 > timeout_ns) {
+            set_status(&ctrl->status, PIP_ETIMEOUT);
+            bad = 1;
+            break;
+          }
         }
       }
-      if (__shfl_sync(0xffffffffu, bad, 0)) {
-        *fail = 1u;
-        return 0;
-      }
+    }
+    if (__shfl_sync(0xffffffffu, bad, 0)) {
+      *fail = 1u;
+      return 0;
     }
   }
   return prefix;
 }
 
-// One pass over tiles of kItems elements (kItems / kScanThreads per thread).
-// Block b takes tiles b, b + G, b + 2G, ... (G = grid size, every block
-// resident), with two tile buffers so that the next tile's bulk load
-// overlaps the current tile's scan and write-back.
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// One pass over tiles of kItems elements, kPer consecutive elements per
+// scanning thread.  Block b takes its m tiles b, b + G, ... (G = grid size,
+// every block resident); its local tile i sits in buffer i % kStages.  Per
+// local tile i the scanning threads
+//   issue the copy of tile i + kAhead (into the buffer of tile i - 2, once
+//   that tile's store has read it), wait for tile i, scan it into registers,
+//   publish its sum,                                       -- then handoff H(i)
+//   finish tile i - 1: add the prefix the look-back warp found for it, write
+//   it to its buffer and store it,
+// and the look-back warp, between H(i) and H(i + 1), finds tile i's prefix.
+// A failed wait (status set) never changes which copies are issued or
+// awaited; it only turns later look-backs into no-ops (the output is then
+// unspecified), so the block always drains its copies before it exits.
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(T* A, uint64_t n, T* total_out, ScanCtrl* ctrl,
-                                                            ScanDesc* ring, uint64_t timeout_ns, uint32_t* latch) {
+__global__ void __launch_bounds__(kBlockThreads, 1)
+    scan_kernel(T* A, uint64_t n, T* total_out, ScanCtrl* ctrl, ScanDesc* ring, uint64_t timeout_ns,
+                uint32_t* latch) {
   constexpr uint32_t kItems = kTileBytes / sizeof(T);
   constexpr uint32_t kPer = kItems / kScanThreads;
+  constexpr uint32_t kVec = 16u / sizeof(T);  // elements per 16-byte access
+  static_assert(kPer * kScanThreads == kItems && kPer % kVec == 0, "tile shape");
   extern __shared__ __align__(128) unsigned char s_raw[];
-  T* const s_buf = reinterpret_cast<T*>(s_raw);  // two tiles of kItems
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ T s_warp[kScanThreads / 32];
-  __shared__ T s_prefix;
-  __shared__ uint32_t s_fail;
+  T* const s_buf = reinterpret_cast<T*>(s_raw);  // kStages tiles of kItems
+  __shared__ __align__(8) uint64_t s_bar[kStages];
+  __shared__ T s_warp[kScanThreads / 32u];
+  __shared__ T s_agg[2];  // tile sums, scanning threads -> look-back warp
+  __shared__ T s_pre[2];  // tile prefixes, look-back warp -> scanning threads
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint64_t ntiles = (n + kItems - 1) / kItems;
-  const uint64_t G = gridDim.x;
+  const uint64_t G = gridDim.x, blk = blockIdx.x;
+  const uint64_t m = blk < ntiles ? (ntiles - 1 - blk) / G + 1 : 0;  // this block's tiles
   if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    s_fail = 0;
+    for (uint32_t q = 0; q < kStages; ++q) mbar_init(&s_bar[q], 1);
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
-  // starts the bulk load of tile u into buffer b (full tiles; the ragged last
-  // one is read with plain loads when it is processed)
-  auto start_load = [&](uint64_t u, uint32_t b) {
-    if (tid == 0 && u < ntiles && (u + 1) * kItems <= n) {
-      mbar_expect_tx(&s_bar[b], kTileBytes);
-      bulk_load(s_buf + b * kItems, A + u * kItems, kTileBytes, &s_bar[b]);
-    }
-  };
-  uint32_t phase[2] = {0u, 0u};
-  uint32_t b = 0;
-  start_load(blockIdx.x, 0);
-  for (uint64_t t = blockIdx.x; t < ntiles; t += G, b ^= 1u) {
-    T* const tile = s_buf + b * kItems;
-    // the other buffer's bulk store has read its source, then the next
-    // tile's load starts there
-    if (tid == 0) bulk_wait_read();
-    start_load(t + G, b ^ 1u);
-    const uint64_t base = t * kItems;
-    const bool full = base + kItems <= n;
-    const uint32_t cnt = full ? kItems : (uint32_t)(n - base);
-    if (full) {
-      if (!mbar_wait(&s_bar[b], phase[b], timeout_ns)) {
-        set_status(&ctrl->status, PIP_ETIMEOUT);
-        s_fail = 1u;
-      }
-      phase[b] ^= 1u;
-    } else {
-      for (uint32_t j = tid; j < kItems; j += kScanThreads) tile[j] = j < cnt ? ldcg(A + base + j) : T(0);
-    }
-    __syncthreads();
-    if (s_fail != 0u) break;
-    // ---- scan: each thread its kPer consecutive elements, then the block
-    T v[kPer];
-    T run = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-      v[k] = run;
-      run += tile[tid * kPer + k];
-    }
-    const T incl = warp_incl_scan(run, lane);
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const T w = lane < kScanThreads / 32 ? s_warp[lane] : T(0);
-      const T wi = warp_incl_scan(w, lane);
-      if (lane < kScanThreads / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
-      const T agg = __shfl_sync(0xffffffffu, wi, 31);       // the tile's sum
-      ScanDesc* d = ring + (t & (kRing - 1));
+
+  if (warp == kScanThreads / 32u) {
+    // ---- the look-back warp
+    bool failed = false;
+    for (uint64_t i = 0;; ++i) {
+      named_sync(kBarHandoff, kBlockThreads);  // H(i)
+      if (i >= m) break;
+      const uint64_t t = blk + i * G;
+      const T agg = s_agg[i & 1u];
       T prefix = 0;
-      if (t == 0) {
-        if (lane == 0) desc_publish<T>(d, t, kFlagPrefix, agg);
-      } else {
-        if (lane == 0) desc_publish<T>(d, t, kFlagAgg, agg);
+      if (t > 0 && !failed) {
         uint32_t fail = 0;
         prefix = look_back<T>(ring, t, lane, ctrl, timeout_ns, &fail);
-        if (fail) {
-          if (lane == 0) s_fail = 1u;
-        } else if (lane == 0) {
-          desc_publish<T>(d, t, kFlagPrefix, (T)(prefix + agg));
-        }
+        failed = fail != 0u;
+        if (!failed && lane == 0) desc_publish<T>(ring + (t & (kRing - 1)), t, kFlagPrefix, (T)(prefix + agg));
       }
       if (lane == 0) {
-        s_prefix = prefix;
+        s_pre[i & 1u] = prefix;
         if (t == ntiles - 1 && total_out != nullptr) stcg(total_out, (T)(prefix + agg));
       }
     }
-    __syncthreads();
-    if (s_fail != 0u) break;
-    // ---- write the exclusive prefixes back (every thread has read its
-    // inputs, so the tile is overwritten in place)
-    const T off = s_prefix + s_warp[warp] + (incl - run);
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) tile[tid * kPer + k] = off + v[k];
-    if (full) {
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) bulk_store(A + base, tile, kTileBytes);
-    } else {
-      __syncthreads();
-      for (uint32_t j = tid; j < cnt; j += kScanThreads) stcg(A + base + j, tile[j]);
+    return;
+  }
+
+  // ---- the scanning threads
+  auto full_tile = [&](uint64_t u) { return (u + 1) * kItems <= n; };
+  // thread 0 issues every copy (bulk groups are per thread)
+  auto start_load = [&](uint64_t i) {
+    const uint64_t u = blk + i * G;
+    if (i < m && full_tile(u)) {
+      uint64_t* bar = &s_bar[i % kStages];
+      mbar_expect_tx(bar, kTileBytes);
+      bulk_load(s_buf + (i % kStages) * kItems, A + u * kItems, kTileBytes, bar);
     }
-    __syncthreads();
+  };
+  if (tid == 0)
+    for (uint32_t i = 0; i < kAhead; ++i) start_load(i);
+  T vprev[kPer];
+  T offprev = 0;
+  uint64_t tprev = 0;
+  for (uint64_t i = 0; i <= m; ++i) {
+    T vcur[kPer];
+    T offcur = 0;
+    const uint64_t t = blk + i * G;
+    if (i < m) {
+      // the buffer of tile i + kAhead last held tile i - 2, stored at the
+      // end of the previous step
+      if (tid == 0) {
+        bulk_wait_read();
+        start_load(i + kAhead);
+      }
+      const uint64_t base = t * kItems;
+      T run = 0;
+      if (full_tile(t)) {
+        if (!mbar_wait(&s_bar[i % kStages], (uint32_t)((i / kStages) & 1u), timeout_ns))
+          set_status(&ctrl->status, PIP_ETIMEOUT);
+        const uint4* src = reinterpret_cast<const uint4*>(s_buf + (i % kStages) * kItems + tid * kPer);
+#pragma unroll
+        for (uint32_t q = 0; q < kPer / kVec; ++q) {
+          const uint4 w = src[q];
+          const T* e = reinterpret_cast<const T*>(&w);
+#pragma unroll
+          for (uint32_t k = 0; k < kVec; ++k) {
+            vcur[q * kVec + k] = run;
+            run += e[k];
+          }
+        }
+      } else {  // the ragged last tile, read with plain loads
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+          const uint64_t g = base + tid * kPer + k;
+          vcur[k] = run;
+          if (g < n) run += ldcg(A + g);
+        }
+      }
+      const T incl = warp_incl_scan(run, lane);
+      if (lane == 31u) s_warp[warp] = incl;
+      named_sync(kBarScan, kScanThreads);
+      T woff = 0, agg = 0;
+#pragma unroll
+      for (uint32_t w = 0; w < kScanThreads / 32u; ++w) {
+        const T x = s_warp[w];
+        agg += x;
+        if (w < warp) woff += x;
+      }
+      offcur = woff + (incl - run);
+      if (tid == 0) {
+        desc_publish<T>(ring + (t & (kRing - 1)), t, t == 0 ? kFlagPrefix : kFlagAgg, agg);
+        s_agg[i & 1u] = agg;
+      }
+    }
+    named_sync(kBarHandoff, kBlockThreads);  // H(i)
+    if (i >= 1) {
+      // finish tile i - 1 with the prefix the look-back warp found for it
+      const uint64_t ip = i - 1;
+      const T add = s_pre[ip & 1u] + offprev;
+      const uint64_t base = tprev * kItems;
+      if (full_tile(tprev)) {
+        T* tile = s_buf + (ip % kStages) * kItems;
+        uint4* dst = reinterpret_cast<uint4*>(tile + tid * kPer);
+#pragma unroll
+        for (uint32_t q = 0; q < kPer / kVec; ++q) {
+          uint4 w;
+          T* e = reinterpret_cast<T*>(&w);
+#pragma unroll
+          for (uint32_t k = 0; k < kVec; ++k) e[k] = vprev[q * kVec + k] + add;
+          dst[q] = w;
+        }
+        fence_proxy_async();
+        named_sync(kBarScan, kScanThreads);
+        if (tid == 0) bulk_store(A + base, tile, kTileBytes);
+      } else {
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k) {
+          const uint64_t g = base + tid * kPer + k;
+          if (g < n) stcg(A + g, (T)(vprev[k] + add));
+        }
+      }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) vprev[k] = vcur[k];
+    offprev = offcur;
+    tprev = t;
   }
   if (tid == 0) {
     bulk_wait_all();
@@ -335,9 +454,9 @@ int scan_blocks_per_sm() {
   auto it = cache.find(dev);
   if (it == cache.end()) {
     int per_sm = 0;
-    if (cudaFuncSetAttribute(scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTileBytes) !=
+    if (cudaFuncSetAttribute(scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel<T>, (int)kScanThreads, 2 * kTileBytes) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel<T>, (int)kBlockThreads, kSmemBytes) !=
             cudaSuccess) {
       cudaGetLastError();
       return 0;
@@ -355,12 +474,12 @@ pip_status launch_scan(T* A, uint64_t n, T* total, void* aux, uint64_t timeout_n
   if (per_sm < 1) return PIP_ECUDA;
   uint32_t* latch = error_latch_ptr();
   if (latch == nullptr) return PIP_ECUDA;
-  // at most kRing / 4 - 1 blocks (two tiles in flight each), so that the
-  // ring outlasts every look-back; the tags hold 24 bits of the tile index,
-  // far more than the tiles in flight
+  // at most kRing / 8 blocks, so that the ring outlasts every look-back;
+  // the tags hold 24 bits of the tile index, far more than the tiles in
+  // flight
   const uint64_t ntiles = (n + kTileBytes / sizeof(T) - 1) / (kTileBytes / sizeof(T));
   const uint32_t blocks = (uint32_t)std::max<uint64_t>(
-      1, std::min<uint64_t>({(uint64_t)per_sm * di.sms, (uint64_t)kRing / 4 - 1, ntiles}));
+      1, std::min<uint64_t>({(uint64_t)per_sm * di.sms, (uint64_t)kRing / 8, ntiles}));
   if (cudaMemsetAsync(aux, 0, scan_aux_bytes(), s) != cudaSuccess) return PIP_ECUDA;
   ScanCtrl* ctrl = static_cast<ScanCtrl*>(aux);
   ScanDesc* ring = reinterpret_cast<ScanDesc*>(static_cast<char*>(aux) + sizeof(ScanCtrl));
@@ -368,8 +487,8 @@ pip_status launch_scan(T* A, uint64_t n, T* total, void* aux, uint64_t timeout_n
   // other blocks), which the cooperative launch guarantees
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(kScanThreads);
-  cfg.dynamicSmemBytes = 2 * kTileBytes;
+  cfg.blockDim = dim3(kBlockThreads);
+  cfg.dynamicSmemBytes = kSmemBytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
