@@ -488,6 +488,131 @@ def run_list(args):
     return 0
 
 
+# one rake touches the 32-B sectors of its leaf, parent, sibling and
+# grandparent (read) and writes three of them; an internal node is read once
+# when admitted: (4 + 3) * 32 + 32 bytes per leaf-internal pair
+TREE_BYTES_PER_NODE = 128
+PAPER_TREE_PIP_200M_MS = 680.0  # PIP tree contraction, 200M entries, 72 cores + HT (Table "lt-runtime")
+
+
+def _random_tree_on_device(leaves, seed):
+    """The bench's forest on the GPU: one random binary tree over ``leaves``
+    leaves built bottom-up (the current roots shuffled by torch.randperm and
+    joined in pairs, level after level, depth about log2 of the leaves), then
+    every node id renamed by a uniform permutation -- the construction of
+    workloads.random_tree, drawn with torch's generator."""
+    import torch
+
+    dev = "cuda"
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    n = 2 * leaves - 1
+    par = torch.full((n,), -1, dtype=torch.int64, device=dev)
+    lft = torch.full((n,), -1, dtype=torch.int64, device=dev)
+    rgt = torch.full((n,), -1, dtype=torch.int64, device=dev)
+    roots = torch.arange(leaves, dtype=torch.int64, device=dev)
+    nxt = leaves
+    while roots.numel() > 1:
+        roots = roots[torch.randperm(roots.numel(), device=dev, generator=gen)]
+        k = roots.numel() // 2
+        new = torch.arange(nxt, nxt + k, dtype=torch.int64, device=dev)
+        nxt += k
+        lft[new] = roots[:k]
+        rgt[new] = roots[k:2 * k]
+        par[roots[:k]] = new
+        par[roots[k:2 * k]] = new
+        roots = torch.cat([new, roots[2 * k:]])
+    perm = torch.randperm(n, device=dev, generator=gen)
+
+    def ren(a):
+        return torch.where(a >= 0, perm[a.clamp(min=0)], a)
+
+    rec = torch.empty((n, 4), dtype=torch.int64, device=dev)
+    rec[perm, 0] = ren(par)
+    rec[perm, 1] = ren(lft)
+    rec[perm, 2] = ren(rgt)
+    rec[:, 3] = 0
+    del par, lft, rgt, perm, roots
+    return rec
+
+
+def run_tree(args):
+    """Tree contraction (Section 4.2): a random binary tree of n = 2L - 1
+    nodes of 32 bytes (the paper's inputs hold 10 to 200 million entries),
+    contracted by rounds over a prefix of the nodes.  The tree is restored
+    before every step (outside the timed region) because contraction
+    consumes it; the last step's output is checked on a sample: each sampled
+    raked leaf's parent still lists the leaf and the recorded sibling as its
+    children, and one leaf is left as the root."""
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    leaves, eps = args.n, args.eps
+    base = _random_tree_on_device(leaves, args.seed)
+    n = base.shape[0]
+    nodes = torch.empty_like(base)
+    opts = {}
+    if args.fresh:
+        opts["fresh_per_round"] = args.fresh
+    if args.block_threads:
+        opts["block_threads"] = args.block_threads
+    plan = pip.tree_plan(n, eps, **opts)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        nodes.copy_(base)
+        pip.tree_contract(nodes, eps=eps, **opts)
+    pip.check()
+    times = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            nodes.copy_(base)
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            pip.tree_contract(nodes, eps=eps, **opts)
+            e_.record(stream)
+            e_.synchronize()
+            times.append(s_.elapsed_time(e_))
+    pip.check()
+    st_buf = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    nodes.copy_(base)
+    pip.tree_contract(nodes, eps=eps, stats=st_buf, **opts)
+    pip.check()
+    st = pip.read_stats(st_buf)
+    leaf = base[:, 1] < 0
+    raked = leaf & (nodes[:, 1] >= 0)
+    idx = torch.nonzero(raked).flatten()
+    idx = idx[::max(1, idx.numel() // 100000)]
+    p, s_ = nodes[idx, 0], nodes[idx, 1]
+    kids = nodes[p][:, 1:3]
+    ok = bool(torch.all(((kids[:, 0] == idx) & (kids[:, 1] == s_)) | ((kids[:, 1] == idx) & (kids[:, 0] == s_))))
+    ok = ok and int((leaf & ~raked).sum()) == 1 and int(raked.sum()) == leaves - 1
+    ms = sorted(times)[len(times) // 2]
+    ach = TREE_BYTES_PER_NODE * n / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    line = {
+        "metric": "contracted tree nodes/s", "value": n / (ms / 1e3), "unit": "nodes/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"tree_contraction_n{n}_one_random_binary_tree_eps{eps}", "n": n, "leaves": leaves,
+                   "eps": eps, "record": "4 x 64-bit words (parent, left, right, round)",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_node": TREE_BYTES_PER_NODE},
+        "plan": {k: plan[k] for k in ("fresh_per_round", "max_active", "grid_blocks", "block_threads", "aux_bytes",
+                                      "smem_bytes", "aux_bound_bytes", "min_rounds")},
+        "rounds": st.rounds, "carried_fraction": st.losers / max(1, st.attempts),
+        "sample_check": ok,
+        "paper_context": {"pip_72cores_ht_200M_ms": PAPER_TREE_PIP_200M_MS},
+        "gpu_launches": args.steps, "clocks": clk.summary(), "step_ms": times,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 SCAN_BYTES_PER_ELEM = {"u32": 8, "u64": 16}  # each element read once and written once
 
 
@@ -690,7 +815,8 @@ def main():
     ap.add_argument("--grid-blocks", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--flags", type=int, default=0, help="PIP_FLAG_* bits (2 = L2 prefetch of the next block)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "floor", "list", "scan"])
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch", "serve", "floor", "list", "tree", "scan"])
     ap.add_argument("--batch-count", type=int, default=8192)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--requests", type=int, default=1000)
@@ -717,6 +843,10 @@ def main():
         if args.n == 10**9:
             args.n = 2 * 10**8  # the paper's largest list
         return run_list(args)
+    if args.workload == "tree":
+        if args.n == 10**9:
+            args.n = 10**8  # leaves: 2 * 10^8 - 1 nodes, the paper's largest tree input
+        return run_tree(args)
 
     import torch
 

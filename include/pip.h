@@ -73,7 +73,7 @@ typedef struct {
     uint64_t aux_bytes;        /* exact device scratch bytes this plan allocates */
     uint64_t aux_bound_bytes;  /* c*n^(1-eps) + 4096 with c = PIP_AUX_C: the bound aux_bytes obeys */
     uint64_t min_rounds;       /* ceil((n-1)/F): a lower bound on the rounds */
-    uint32_t driver;           /* 0 = persistent grid, 1 = one block, 2 = one cluster (shared-memory tables) */
+    uint32_t driver;           /* 0 = persistent grid, 1 = one block, 2 = one cluster (shared-memory tables), 3 = list contraction, 4 = tree contraction */
     uint32_t pad;
     uint64_t smem_bytes;       /* on-chip scratch of the one-block driver (counted in the bound) */
 } pip_plan_info;
@@ -450,6 +450,69 @@ pip_status pip_list_contract_ex(pip_list_node *nodes_dev, uint64_t n, double eps
  * elem_bytes = 16, fresh_per_round, max_active, grid_blocks, block_threads,
  * aux_bytes, smem_bytes, aux_bound_bytes, min_rounds; driver = 3. */
 pip_status pip_list_plan(uint64_t n, double eps, const pip_options *opt, pip_plan_info *out);
+
+/* ------------------------------------------------------------ tree contraction */
+
+/* One node of a forest of rooted binary trees (32 bytes): its parent and its
+ * two children, PIP_TREE_NIL where there is none (a leaf has no children, a
+ * root no parent, and every other node exactly two children); `round` is
+ * written for raked leaves only (see pip_tree_contract). */
+typedef struct {
+    uint64_t parent;
+    uint64_t left;
+    uint64_t right;
+    uint64_t round;
+} pip_tree_node;
+#define PIP_TREE_NIL 0xFFFFFFFFFFFFFFFFull
+
+/*
+ * pip_tree_contract -- in-place tree contraction (Section 4.2, the tree
+ * contraction paragraph), relaxed-PIP by the Decomposable Property: every
+ * round works on a prefix of about C * n^(1-eps) nodes in index order, so the
+ * device scratch stays within PIP_AUX_C * n^(1-eps) + 4096 bytes.
+ *   nodes_dev: device array of n records (32-byte aligned) describing a
+ *              forest of rooted binary trees over the nodes 0..n-1 in which
+ *              every internal node has two children.
+ *   n        : node count, n < 2^32 - 1.  n <= 1 is a no-op.
+ * Raking a leaf l with parent p removes l and p: the other child s of p takes
+ * p's place under p's parent g (or becomes a root).  Node i has priority i.
+ * Round r (from 1) works on the leaves carried from round r-1 plus the next
+ * fn = min(F, nodes not yet admitted, kmax - m + 1) node indices, F and kmax
+ * those of pip_tree_plan (fresh_per_round, max_active) and m the previous
+ * round's active count; internal nodes and parentless leaves in it need no
+ * work.  An active leaf with a parent is raked in the round exactly when no
+ * leaf among its sibling, its nephews (the sibling's children) and its uncle
+ * (the other child of its grandparent) has a smaller index, decided on the
+ * state at the start of the round; so no two rakes of a round touch the same
+ * word and no parent-child pair is contracted in one round.  On return every
+ * tree has one leaf left, as a root; a raked leaf's record holds
+ * (parent = p, left = s, right = g, round = r) as they were at its rake; a
+ * removed internal node keeps the record it had when it was removed.  The
+ * rounds (and so the result) depend on F and kmax only, never on the launch.
+ * Errors (reported by pip_check()): a pointer out of range, or a parent that
+ * does not list the node as a child, stops the run with PIP_EINVAL before
+ * any access outside the array (the records are then unspecified).  Other
+ * inconsistent input gives unspecified records.  With
+ * PIP_FLAG_VALIDATE_INPUT in pip_tree_contract_ex the whole input is checked
+ * first and rejected untouched (PIP_EINVAL).
+ * Scratch is allocated with cudaMallocAsync on `stream` and freed the same way.
+ */
+pip_status pip_tree_contract(pip_tree_node *nodes_dev, uint64_t n, double eps, void *stream);
+
+/* pip_tree_contract_ex -- the same with overrides (opt: prefix_c,
+ * fresh_per_round, grid_blocks, block_threads up to 512, wait_timeout_ns,
+ * flags), caller-provided scratch (aux_dev of at least pip_tree_plan's
+ * aux_bytes, 256-byte aligned, or NULL) and a device pip_stats the kernel
+ * fills (or NULL; attempts counts active nodes over all rounds, losers the
+ * leaves carried to a next round). */
+pip_status pip_tree_contract_ex(pip_tree_node *nodes_dev, uint64_t n, double eps, const pip_options *opt,
+                                void *aux_dev, uint64_t aux_bytes, pip_stats *stats_dev, void *stream);
+
+/* pip_tree_plan -- the plan pip_tree_contract_ex would use (host only):
+ * elem_bytes = 32, fresh_per_round (F), max_active (kmax), grid_blocks,
+ * block_threads, aux_bytes, smem_bytes, aux_bound_bytes, min_rounds;
+ * driver = 4. */
+pip_status pip_tree_plan(uint64_t n, double eps, const pip_options *opt, pip_plan_info *out);
 
 /* ------------------------------------------------------------ scan */
 

@@ -255,6 +255,12 @@ def lib() -> ctypes.CDLL:
         L.pip_list_contract_ex.restype = i32
         L.pip_list_plan.argtypes = [u64, dbl, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
         L.pip_list_plan.restype = i32
+        L.pip_tree_contract.argtypes = [vp, u64, dbl, vp]
+        L.pip_tree_contract.restype = i32
+        L.pip_tree_contract_ex.argtypes = [vp, u64, dbl, ctypes.POINTER(Options), vp, u64, vp, vp]
+        L.pip_tree_contract_ex.restype = i32
+        L.pip_tree_plan.argtypes = [u64, dbl, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
+        L.pip_tree_plan.restype = i32
         L.pip_scan.argtypes = [vp, u64, i32, vp, vp]
         L.pip_scan.restype = i32
         L.pip_scan_ex.argtypes = [vp, u64, i32, vp, vp, u64, vp]
@@ -585,6 +591,44 @@ def list_contract(nodes, eps: float = 0.5, *, stream=None, aux=None, stats=None,
     rc = lib().pip_list_contract_ex(nodes.data_ptr(), nodes.shape[0], eps, _opt_ptr(make_options(**options)),
                                     aux_ptr, aux_n, st_ptr, _stream_handle(stream))
     _raise(rc, "pip_list_contract_ex")
+
+
+# ------------------------------------------------------------------ tree contraction
+TREE_NIL = 0xFFFFFFFFFFFFFFFF
+DRIVER_TREE = 4
+
+
+def tree_plan(n: int, eps: float, **options) -> dict:
+    """The plan pip_tree_contract_ex would use (host only); its
+    fresh_per_round and max_active are the F and kmax of the round schedule."""
+    info = PlanInfo()
+    o = make_options(**options)
+    _raise(lib().pip_tree_plan(n, eps, _opt_ptr(o), ctypes.byref(info)), "pip_tree_plan")
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+
+def tree_contract(nodes, eps: float = 0.5, *, stream=None, aux=None, stats=None, **options) -> None:
+    """Contract the forest in ``nodes`` in place (asynchronous on ``stream``).
+
+    ``nodes``: contiguous CUDA tensor of shape (n, 4) with 8-byte elements
+    (int64 or uint64 bit patterns) holding (parent, left, right, round), -1 /
+    2^64-1 for a missing pointer, 32-byte aligned.  On return every raked leaf
+    holds (parent, sibling, grandparent, round) from its rake, one leaf per
+    tree is left as a root and removed internal nodes keep their last record.
+    ``aux``, ``stats`` and the keyword options are as in :func:`shuffle`.
+    """
+    if not nodes.is_cuda or not nodes.is_contiguous() or nodes.dim() != 2 or nodes.shape[1] != 4 \
+            or nodes.element_size() != 8:
+        raise ValueError("nodes must be a contiguous (n, 4) CUDA tensor of 8-byte elements")
+    aux_ptr, aux_n = (aux.data_ptr(), aux.numel() * aux.element_size()) if aux is not None else (None, 0)
+    st_ptr = None
+    if stats is not None:
+        if stats.numel() * stats.element_size() < STATS_BYTES:
+            raise ValueError("stats buffer too small")
+        st_ptr = stats.data_ptr()
+    rc = lib().pip_tree_contract_ex(nodes.data_ptr(), nodes.shape[0], eps, _opt_ptr(make_options(**options)),
+                                    aux_ptr, aux_n, st_ptr, _stream_handle(stream))
+    _raise(rc, "pip_tree_contract_ex")
 
 
 # ------------------------------------------------------------------ scan

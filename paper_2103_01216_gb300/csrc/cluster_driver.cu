@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(1024) cluster_rounds_kernel(const ClusterArgs 
   const uint64_t t_start = globaltimer_ns();
   // an invalid explicit target sequence was reported by the validation pass
   // (every CTA reads the same word, so all leave together)
-  if (ld_relaxed_u32(&a.ctrl->status) != 0u) {
+  if (block_status(&a.ctrl->status) != 0u) {
     if (rank == 0 && tid == 0) {
       atomicCAS(a.latch, 0u, ld_relaxed_u32(&a.ctrl->status));
       if (a.stats != nullptr) a.stats->status = ld_relaxed_u32(&a.ctrl->status);

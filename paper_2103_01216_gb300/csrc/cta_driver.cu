@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(1024) cta_batch_kernel(const BatchHeader* hdr,
   BatchHeader* h = const_cast<BatchHeader*>(hdr);
   const uint64_t t_start = globaltimer_ns();
   // explicit targets are validated before this launch; stop on a reported error
-  if (ld_relaxed_u32(&h->status) != 0u) return;
+  if (block_status(&h->status) != 0u) return;
   for (;;) {
     if (threadIdx.x == 0) s_job = atomicAdd(&h->next, 1u);
     __syncthreads();
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(1024) cta_single_kernel(const BatchJob job, ui
                                                          uint32_t flags) {
   extern __shared__ uint32_t smem[];
   __shared__ pip_job_stats s_st;
-  if (ld_relaxed_u32(&ctrl->status) != 0u) {  // invalid explicit targets
+  if (block_status(&ctrl->status) != 0u) {  // invalid explicit targets
     if (threadIdx.x == 0) {
       atomicCAS(latch, 0u, ld_relaxed_u32(&ctrl->status));
       if (stats != nullptr) stats->status = ld_relaxed_u32(&ctrl->status);

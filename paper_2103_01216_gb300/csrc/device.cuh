@@ -103,6 +103,19 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// The status word as one value for the whole block: thread 0 reads it and
+// shares it.  A decision that changes a block's control flow around a
+// barrier must be taken from this, never from each thread's own read: a word
+// that another block sets while this block's warps read it would otherwise
+// send part of the block past a __syncthreads the rest still waits at.
+__device__ __forceinline__ uint32_t block_status(const uint32_t* status) {
+  __shared__ uint32_t s_block_status;
+  __syncthreads();  // earlier readers of s_block_status are done
+  if (threadIdx.x == 0) s_block_status = ld_relaxed_u32(status);
+  __syncthreads();
+  return s_block_status;
+}
+
 // Records the first error of a run; later errors are dropped.
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t code) {
   atomicCAS(status, 0u, code);

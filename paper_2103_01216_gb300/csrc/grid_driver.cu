@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
   __shared__ uint32_t s_L, s_Lprev, s_g, s_m, s_stop;
   // run statistics and the deadline, kept by thread 0 (block 0's are reported)
   __shared__ unsigned long long s_attempts, s_losers, s_deadline;
-  __shared__ uint32_t s_max_active, s_rounds;
+  __shared__ uint32_t s_max_active, s_rounds, s_start_status;
 
   Elem* A = static_cast<Elem*>(a.A);
   Ctrl* ctrl = a.ctrl;
@@ -188,10 +188,12 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
     s_g = 0;
     s_m = min(a.F, a.n - 1u);
     s_stop = 0;
+    // an invalid explicit target sequence reported by the validation pass
+    // (read once for the block, so that the whole block leaves together)
+    s_start_status = ld_relaxed_u32(&ctrl->status);
   }
   __syncthreads();
-  // an invalid explicit target sequence was reported by the validation pass
-  if (ld_relaxed_u32(&ctrl->status) != 0u) goto done;
+  if (s_start_status != 0u) goto done;
 
   // ---- prologue: W_0 reserves for round 0 (barrier 0 uses word bw[0];
   // round r's barrier uses bw[(r+1)%3])

@@ -173,8 +173,16 @@ struct ListPlan {
   uint64_t smem_bytes = 0;  // all blocks' on-chip lists (counted in the bound)
   uint64_t aux_bound = 0;
 };
-pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out);
+// The shape of a round-engine plan depends on its kernel's occupancy:
+// blocks_per_sm(threads, kloc) gives it (the list kernel's when null).
+pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out,
+                          int (*blocks_per_sm)(uint32_t threads, uint32_t kloc) = nullptr);
 pip_status launch_list_driver(const ListPlan& plan, void* rec, void* aux, pip_stats* stats, cudaStream_t stream);
+
+// Tree contraction (tree_driver.cu): the plan is a ListPlan made with the
+// tree kernel's occupancy.
+pip_status make_tree_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out);
+pip_status launch_tree_driver(const ListPlan& plan, void* rec, void* aux, pip_stats* stats, cudaStream_t stream);
 
 // Scan (scan.cu): bytes of the fixed scratch (control block and descriptor ring).
 uint64_t scan_aux_bytes();

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kListThreads, PIP_LIST_MIN_BLOCKS) list_rounds
   __shared__ uint32_t s_lcount, s_err;
   __shared__ uint32_t s_U, s_f, s_g, s_m, s_stop;
   __shared__ unsigned long long s_attempts, s_losers, s_deadline;
-  __shared__ uint32_t s_max_active, s_rounds;
+  __shared__ uint32_t s_max_active, s_rounds, s_start_status;
 
   Ctrl* ctrl = a.ctrl;
   ulonglong2* rec = a.rec;
@@ -109,9 +109,12 @@ __global__ void __launch_bounds__(kListThreads, PIP_LIST_MIN_BLOCKS) list_rounds
     s_g = 0;
     s_m = s_f;
     s_stop = 0;
+    // invalid input found by the validation pass (read once for the block,
+    // so that the whole block leaves together)
+    s_start_status = ld_relaxed_u32(&ctrl->status);
   }
   __syncthreads();
-  if (ld_relaxed_u32(&ctrl->status) != 0u) goto done;  // invalid input found by the validation pass
+  if (s_start_status != 0u) goto done;
 
   for (uint32_t r = 0;; ++r) {
     // barrier numbering: phase A of round r ends at barrier 2r+1, phase B at
@@ -317,7 +320,8 @@ int list_blocks_per_sm(uint32_t threads, uint32_t kloc) {
 
 // Plan of one list contraction: prefix F within the scratch bound, grid shape,
 // scratch layout (Ctrl, then two overflow queues of kmax words).
-pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out) {
+pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out,
+                          int (*blocks_per_sm)(uint32_t threads, uint32_t kloc)) {
   if (!(eps > 0.0 && eps < 1.0) || n < 2 || n >= 0xFFFFFFFFull) return PIP_EINVAL;
   pip_options o{};
   if (opt != nullptr) o = *opt;
@@ -342,7 +346,7 @@ pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPl
     if (o.grid_blocks) want_b = o.grid_blocks;
     want_b = std::max<uint64_t>(1, std::min<uint64_t>(want_b, 1023));
     p.kloc = (uint32_t)std::min<uint64_t>(4096, std::max<uint64_t>(32, ((F / 4 + want_b - 1) / want_b + 31) / 32 * 32));
-    const int per_sm = have_dev ? list_blocks_per_sm(threads, p.kloc) : 0;
+    const int per_sm = !have_dev ? 0 : (blocks_per_sm ? blocks_per_sm(threads, p.kloc) : list_blocks_per_sm(threads, p.kloc));
     if (per_sm > 0) want_b = std::min<uint64_t>(want_b, (uint64_t)per_sm * di.sms);
     p.blocks = (uint32_t)want_b;
     // every block handles at most kMaxSlots items per thread and round
