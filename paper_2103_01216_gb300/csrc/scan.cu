@@ -46,12 +46,16 @@ namespace pip {
 namespace {
 
 // Shape: kStages tile buffers of PIP_SCAN_TILE_KB each (one block per SM),
-// PIP_SCAN_THREADS scanning threads plus the look-back warp.
+// PIP_SCAN_THREADS scanning threads plus the look-back warp.  Four 56 KB
+// buffers (two copies ahead) and 512 scanning threads measured best on GB300
+// at 10^9 elements: 75 % (u64) and 81 % (u32) of the HBM copy bandwidth,
+// against 74-77 % for 48 KB, 71 % for 40 KB x 5, 54-57 % for 32 KB x 6,
+// 53-54 % for 64 KB x 3 (one copy ahead) and 60-65 % for 768 threads.
 #ifndef PIP_SCAN_THREADS
 #define PIP_SCAN_THREADS 512
 #endif
 #ifndef PIP_SCAN_TILE_KB
-#define PIP_SCAN_TILE_KB 48
+#define PIP_SCAN_TILE_KB 56
 #endif
 #ifndef PIP_SCAN_STAGES
 #define PIP_SCAN_STAGES 4

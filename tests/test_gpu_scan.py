@@ -31,7 +31,7 @@ def expected(a: np.ndarray):
     return b, t
 
 
-TILE = {np.uint32: 8192, np.uint64: 4096}
+TILE = {np.uint32: 14336, np.uint64: 7168}  # elements per 56 KB tile
 
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
