@@ -170,13 +170,17 @@ struct ListPlan {
   uint64_t deadline_ns = 0;
   uint64_t off_Q[2] = {0, 0};
   uint64_t aux_bytes = 0;
-  uint64_t smem_bytes = 0;  // all blocks' on-chip lists (counted in the bound)
+  uint64_t smem_bytes = 0;  // all blocks' on-chip lists and caches (counted in the bound)
   uint64_t aux_bound = 0;
+  uint32_t cache_per_thread = 0;  // bytes of on-chip cache per thread (tree contraction)
+  uint64_t block_smem() const { return 8ull * kloc + (uint64_t)cache_per_thread * threads; }
 };
 // The shape of a round-engine plan depends on its kernel's occupancy:
-// blocks_per_sm(threads, kloc) gives it (the list kernel's when null).
+// blocks_per_sm(threads, dynamic shared bytes) gives it (the list kernel's
+// when null); cache_per_thread adds on-chip bytes per thread to each block.
 pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out,
-                          int (*blocks_per_sm)(uint32_t threads, uint32_t kloc) = nullptr);
+                          int (*blocks_per_sm)(uint32_t threads, uint64_t smem) = nullptr,
+                          uint32_t cache_per_thread = 0);
 pip_status launch_list_driver(const ListPlan& plan, void* rec, void* aux, pip_stats* stats, cudaStream_t stream);
 
 // Tree contraction (tree_driver.cu): the plan is a ListPlan made with the

@@ -293,21 +293,21 @@ __global__ void validate_list_kernel(const ulonglong2* __restrict__ rec, uint32_
 
 uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
 
-int list_blocks_per_sm(uint32_t threads, uint32_t kloc) {
+int list_blocks_per_sm(uint32_t threads, uint64_t smem) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   static std::mutex mu;
-  static std::map<std::tuple<int, uint32_t, uint32_t>, int> cache;
+  static std::map<std::tuple<int, uint32_t, uint64_t>, int> cache;
   std::lock_guard<std::mutex> lk(mu);
-  const auto key = std::make_tuple(dev, threads, kloc);
+  const auto key = std::make_tuple(dev, threads, smem);
   auto it = cache.find(key);
   if (it == cache.end()) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, list_rounds_kernel, (int)threads,
-                                                      (size_t)8 * kloc) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, list_rounds_kernel, (int)threads, (size_t)smem) !=
+        cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -321,7 +321,7 @@ int list_blocks_per_sm(uint32_t threads, uint32_t kloc) {
 // Plan of one list contraction: prefix F within the scratch bound, grid shape,
 // scratch layout (Ctrl, then two overflow queues of kmax words).
 pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out,
-                          int (*blocks_per_sm)(uint32_t threads, uint32_t kloc)) {
+                          int (*blocks_per_sm)(uint32_t threads, uint64_t smem), uint32_t cache_per_thread) {
   if (!(eps > 0.0 && eps < 1.0) || n < 2 || n >= 0xFFFFFFFFull) return PIP_EINVAL;
   pip_options o{};
   if (opt != nullptr) o = *opt;
@@ -332,6 +332,7 @@ pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPl
   uint32_t threads = o.block_threads ? o.block_threads : kListThreads;
   if (threads < 128 || threads > kListThreads || threads % 32 != 0) return PIP_EINVAL;
   p.threads = threads;
+  p.cache_per_thread = cache_per_thread;
   DeviceInfo di;
   const bool have_dev = device_info(&di) == PIP_OK;
   double want = o.fresh_per_round ? (double)o.fresh_per_round : (o.prefix_c > 0.0 ? o.prefix_c : 4.0) * x;
@@ -346,7 +347,8 @@ pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPl
     if (o.grid_blocks) want_b = o.grid_blocks;
     want_b = std::max<uint64_t>(1, std::min<uint64_t>(want_b, 1023));
     p.kloc = (uint32_t)std::min<uint64_t>(4096, std::max<uint64_t>(32, ((F / 4 + want_b - 1) / want_b + 31) / 32 * 32));
-    const int per_sm = !have_dev ? 0 : (blocks_per_sm ? blocks_per_sm(threads, p.kloc) : list_blocks_per_sm(threads, p.kloc));
+    const int per_sm =
+        !have_dev ? 0 : (blocks_per_sm ? blocks_per_sm(threads, p.block_smem()) : list_blocks_per_sm(threads, p.block_smem()));
     if (per_sm > 0) want_b = std::min<uint64_t>(want_b, (uint64_t)per_sm * di.sms);
     p.blocks = (uint32_t)want_b;
     // every block handles at most kMaxSlots items per thread and round
@@ -357,7 +359,7 @@ pip_status make_list_plan(uint64_t n, double eps, const pip_options* opt, ListPl
     p.off_Q[0] = align256(sizeof(Ctrl));
     p.off_Q[1] = p.off_Q[0] + align256(4ull * p.kmax);
     p.aux_bytes = p.off_Q[1] + align256(4ull * p.kmax);
-    p.smem_bytes = (uint64_t)p.blocks * 8ull * p.kloc;
+    p.smem_bytes = (uint64_t)p.blocks * p.block_smem();
     const bool fits = p.aux_bytes + p.smem_bytes <= p.aux_bound && p.kmax <= cap;
     if (fits || F <= 1) break;
     const double ratio = std::min((double)p.aux_bound / (double)(p.aux_bytes + p.smem_bytes),
@@ -398,13 +400,13 @@ pip_status launch_list_driver(const ListPlan& plan, void* rec, void* aux, pip_st
   }
   DeviceInfo di;
   if (device_info(&di) != PIP_OK) return PIP_ECUDA;
-  const int per_sm = list_blocks_per_sm(plan.threads, plan.kloc);
+  const int per_sm = list_blocks_per_sm(plan.threads, plan.block_smem());
   if (per_sm < 1) return PIP_ECUDA;
   const uint32_t blocks = std::max(1u, std::min<uint32_t>({plan.blocks, (uint32_t)per_sm * (uint32_t)di.sms, 1023u}));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(plan.threads);
-  cfg.dynamicSmemBytes = 8ull * plan.kloc;
+  cfg.dynamicSmemBytes = plan.block_smem();
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -39,6 +39,7 @@
 // phase A of the same round.  PIP_FLAG_VALIDATE_INPUT adds a full check of
 // the forest before anything is modified.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -54,6 +55,13 @@ constexpr uint64_t kNil = PIP_TREE_NIL;
 constexpr unsigned kFullT = 0xffffffffu;
 constexpr uint32_t kMaxSlots = 32;  // items per thread and round (one mark bit each)
 constexpr uint32_t kTreeThreads = 512;
+// A marked leaf's sibling and grandparent, found in phase A, are kept on chip
+// for phase B (slots q < kCacheSlots of each thread, two 32-bit words each;
+// which child word of the grandparent to rewrite is a register bit), so that
+// phase B only writes.  Later slots read their records again.
+constexpr uint32_t kCacheSlots = 8;
+constexpr uint32_t kCacheBytesPerThread = 8u * kCacheSlots;
+constexpr uint32_t kNil32 = 0xFFFFFFFFu;
 #ifndef PIP_TREE_MIN_BLOCKS
 #define PIP_TREE_MIN_BLOCKS 2
 #endif
@@ -72,6 +80,7 @@ struct TreeArgs {
   uint64_t timeout_ns;
   uint64_t deadline_ns;
   uint32_t max_rounds;
+  uint32_t qc;  // cached slots per thread (0 or kCacheSlots)
 };
 
 __device__ __forceinline__ uint64_t parent_of(const ulonglong2* h, uint64_t v) { return ldcg(&h[2 * v].x); }
@@ -87,8 +96,11 @@ __device__ __forceinline__ void tree_slice(uint32_t f, uint32_t* off, uint32_t* 
 }
 
 // Phase A for node i: 0 = no work (internal node or root), 1 = rakes this
-// round, 2 = carried; *bad set on a pointer that fails its check.
-__device__ __forceinline__ uint32_t tree_decide(const ulonglong2* h, uint64_t i, uint64_t n, bool* bad) {
+// round, 2 = carried; *bad set on a pointer that fails its check.  For a leaf
+// that rakes, *s_out and *g_out are its sibling and grandparent and *g_right
+// tells that the parent is the grandparent's right child.
+__device__ __forceinline__ uint32_t tree_decide(const ulonglong2* h, uint64_t i, uint64_t n, bool* bad,
+                                                uint64_t* s_out, uint64_t* g_out, bool* g_right) {
   const ulonglong2 me = ldcg(&h[2 * i]);  // (parent, left)
   if (me.y != kNil || me.x == kNil) return 0u;
   const uint64_t p = me.x;
@@ -137,6 +149,9 @@ __device__ __forceinline__ uint32_t tree_decide(const ulonglong2* h, uint64_t i,
   const bool l1 = c1 != kNil && left_of(h, c1) == kNil;
   const bool lu = u != kNil && left_of(h, u) == kNil;
   win = win && !l0 && !l1 && !lu;
+  *s_out = s;
+  *g_out = g;
+  *g_right = g != kNil && gr == p;
   return win ? 1u : 2u;
 }
 
@@ -164,7 +179,9 @@ __device__ __forceinline__ bool tree_rake(ulonglong2* h, uint64_t i, uint32_t r,
 }
 
 __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds_kernel(const TreeArgs a) {
-  extern __shared__ uint32_t s_loc[];  // two on-chip lists of a.kloc carried leaves
+  extern __shared__ uint32_t s_loc[];  // two on-chip lists of a.kloc carried leaves, then the cache
+  uint32_t* const c_sib = s_loc + 2u * a.kloc;      // [a.qc][blockDim.x]
+  uint32_t* const c_gp = c_sib + a.qc * blockDim.x;  // [a.qc][blockDim.x]
   __shared__ uint32_t s_nloc[2];
   __shared__ uint32_t s_lcount, s_err;
   __shared__ uint32_t s_U, s_f, s_g, s_m, s_stop;
@@ -230,7 +247,7 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
     if (nslot > kMaxSlots && threadIdx.x == 0) fail(PIP_EINTERNAL);  // the planner keeps this from happening
 
     // ---- phase A: mark the leaves that rake, keep the others
-    uint32_t marks = 0;
+    uint32_t marks = 0, rights = 0;
     for (uint32_t q = 0; q < nslot && q < kMaxSlots; ++q) {
       uint32_t i = 0;
       bool act;
@@ -245,9 +262,15 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
       }
       uint32_t d = 0;
       if (act) {
-        bool bad = false;
-        d = tree_decide(h, i, a.n, &bad);
+        bool bad = false, g_right = false;
+        uint64_t sib = kNil, gp = kNil;
+        d = tree_decide(h, i, a.n, &bad, &sib, &gp, &g_right);
         if (bad) fail(PIP_EINVAL);
+        if (d == 1u && q < a.qc) {
+          c_sib[q * NT + threadIdx.x] = (uint32_t)sib;
+          c_gp[q * NT + threadIdx.x] = gp == kNil ? kNil32 : (uint32_t)gp;
+          if (g_right) rights |= 1u << q;
+        }
       }
       if (d == 1u) marks |= 1u << q;
       const bool keep = d == 2u;
@@ -328,7 +351,26 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
         const uint32_t pq = (q - nfs) * NT + threadIdx.x;
         i = (pq < nloc) ? loc_in[pq] : ldcg(Qg + pq);
       }
-      if (!tree_rake(h, i, r, a.n)) fail(PIP_EINTERNAL);
+      if (q < a.qc) {
+        // cached: only writes (the values were checked in phase A)
+        using u64 = unsigned long long;
+        const uint64_t sib = c_sib[q * NT + threadIdx.x];
+        const uint32_t g32 = c_gp[q * NT + threadIdx.x];
+        const uint64_t gp = g32 == kNil32 ? kNil : (uint64_t)g32;
+        if (sib >= a.n || (gp != kNil && gp >= a.n)) {
+          fail(PIP_EINTERNAL);
+          continue;
+        }
+        stcg(&h[2 * sib].x, (u64)gp);
+        if (gp != kNil) {
+          if ((rights >> q) & 1u) stcg(&h[2 * gp + 1].x, (u64)sib);
+          else stcg(&h[2 * gp].y, (u64)sib);
+        }
+        stcg(&h[2 * (uint64_t)i].y, (u64)sib);
+        stcg(&h[2 * (uint64_t)i + 1], make_ulonglong2((u64)gp, (u64)r + 1ull));
+      } else if (!tree_rake(h, i, r, a.n)) {
+        fail(PIP_EINTERNAL);
+      }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) stcg(&ctrl->bw[(eB + 1u) % 3u], 0ull);  // word of barrier eB+1
     __syncthreads();  // s_err is final
@@ -370,21 +412,37 @@ __global__ void validate_tree_kernel(const ulonglong2* __restrict__ h, uint32_t 
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(&ctrl->status, PIP_EINVAL);
 }
 
-int tree_blocks_per_sm(uint32_t threads, uint32_t kloc) {
+// Resident blocks per SM for a launch of `threads` threads with `smem` bytes
+// of dynamic shared memory (the kernel's limit is raised once to the
+// device's opt-in maximum, so that any planned size is admissible).
+int tree_blocks_per_sm(uint32_t threads, uint64_t smem) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   static std::mutex mu;
-  static std::map<std::tuple<int, uint32_t, uint32_t>, int> cache;
+  static std::map<std::tuple<int, uint32_t, uint64_t>, int> cache;
+  static std::map<int, bool> raised;
   std::lock_guard<std::mutex> lk(mu);
-  const auto key = std::make_tuple(dev, threads, kloc);
+  if (!raised[dev]) {
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, tree_rounds_kernel) != cudaSuccess ||
+        cudaFuncSetAttribute(tree_rounds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    raised[dev] = true;
+  }
+  const auto key = std::make_tuple(dev, threads, smem);
   auto it = cache.find(key);
   if (it == cache.end()) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_rounds_kernel, (int)threads,
-                                                      (size_t)8 * kloc) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_rounds_kernel, (int)threads, (size_t)smem) !=
+        cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -395,8 +453,31 @@ int tree_blocks_per_sm(uint32_t threads, uint32_t kloc) {
 
 }  // namespace
 
+// Bytes of L2 per fresh node of the default prefix: phase A of a round reads
+// the parent, sibling and grandparent records of its leaves (about half of
+// the fresh nodes) at random, and the rounds ran fastest on GB300 (L2 of
+// 129 MB) when those reads about filled L2, at F = 600K (21.8 ms for a tree
+// of 2e8 nodes, against 23.3 ms at 300K and 900K and 24.3 ms at 1.25M).
+constexpr uint64_t kTreeL2BytesPerFresh = 216;
+
+// The list engine's plan, with the phase-B cache when it fits the scratch
+// bound without lowering F (otherwise without it).  Unless the caller fixes
+// F, the default prefix C * n^(1-eps) is also capped at L2 / 216 bytes.
 pip_status make_tree_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out) {
-  return make_list_plan(n, eps, opt, out, &tree_blocks_per_sm);
+  pip_options o{};
+  if (opt != nullptr) o = *opt;
+  DeviceInfo di;
+  if (o.fresh_per_round == 0 && eps > 0.0 && eps < 1.0 && device_info(&di) == PIP_OK && di.l2_bytes > 0) {
+    const double want = (o.prefix_c > 0.0 ? o.prefix_c : 4.0) * std::pow((double)n, 1.0 - eps);
+    const double cap = (double)di.l2_bytes / (double)kTreeL2BytesPerFresh;
+    if (want > cap) o.fresh_per_round = (uint32_t)cap;
+  }
+  ListPlan plain, cached;
+  pip_status st = make_list_plan(n, eps, &o, &plain, &tree_blocks_per_sm, 0);
+  if (st != PIP_OK) return st;
+  st = make_list_plan(n, eps, &o, &cached, &tree_blocks_per_sm, kCacheBytesPerThread);
+  *out = (st == PIP_OK && cached.F == plain.F) ? cached : plain;
+  return PIP_OK;
 }
 
 pip_status launch_tree_driver(const ListPlan& plan, void* rec, void* aux, pip_stats* stats, cudaStream_t stream) {
@@ -416,6 +497,7 @@ pip_status launch_tree_driver(const ListPlan& plan, void* rec, void* aux, pip_st
   a.timeout_ns = plan.timeout_ns;
   a.deadline_ns = plan.deadline_ns;
   a.max_rounds = plan.n + 8u;
+  a.qc = plan.cache_per_thread / 8u;
   if (cudaMemsetAsync(aux, 0, plan.aux_bytes, stream) != cudaSuccess) return PIP_ECUDA;
   if (plan.flags & PIP_FLAG_VALIDATE_INPUT) {
     const uint32_t vb = (uint32_t)std::min<uint64_t>(1024, (plan.n + 255) / 256);
@@ -424,13 +506,13 @@ pip_status launch_tree_driver(const ListPlan& plan, void* rec, void* aux, pip_st
   }
   DeviceInfo di;
   if (device_info(&di) != PIP_OK) return PIP_ECUDA;
-  const int per_sm = tree_blocks_per_sm(plan.threads, plan.kloc);
+  const int per_sm = tree_blocks_per_sm(plan.threads, plan.block_smem());
   if (per_sm < 1) return PIP_ECUDA;
   const uint32_t blocks = std::max(1u, std::min<uint32_t>({plan.blocks, (uint32_t)per_sm * (uint32_t)di.sms, 1023u}));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(plan.threads);
-  cfg.dynamicSmemBytes = 8ull * plan.kloc;
+  cfg.dynamicSmemBytes = plan.block_smem();
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
