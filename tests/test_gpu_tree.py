@@ -224,3 +224,20 @@ def test_large_forest_in_the_bench_launch(pip):
     assert np.array_equal(out, expected(rec, F))
     rc, back = oracle.tree_uncontract(out, rec)
     assert rc == 0 and np.array_equal(back, rec)
+
+
+@pytest.mark.parametrize("opts", [dict(grid_blocks=152, fresh_per_round=400000), dict(grid_blocks=38)])
+def test_phase_b_cache_path(pip, opts):
+    # Plans whose blocks keep the on-chip phase-B cache (64 bytes per thread,
+    # counted in smem_bytes): with 152 blocks every marked leaf's phase B is
+    # writes only; with 38 blocks threads hold more than the eight cached
+    # slots, so the cached and the re-reading paths run in the same rounds.
+    rec = workloads.random_tree((1 << 20) + 7, rng_seed=77, trees=3)
+    n = rec.shape[0]
+    F, plan = plan_F(pip, n, 0.1, **opts)
+    assert plan["smem_bytes"] >= plan["grid_blocks"] * plan["block_threads"] * 64, plan
+    out, st = gpu_contract(pip, rec, eps=0.1, with_stats=True, **opts)
+    assert st.status == 0
+    assert np.array_equal(out, expected(rec, F))
+    rc, back = oracle.tree_uncontract(out, rec)
+    assert rc == 0 and np.array_equal(back, rec)
