@@ -439,6 +439,8 @@ def run_list(args):
         opts["fresh_per_round"] = args.fresh
     if args.block_threads:
         opts["block_threads"] = args.block_threads
+    if args.grid_blocks:
+        opts["grid_blocks"] = args.grid_blocks
     plan = pip.list_plan(n, eps, **opts)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -560,6 +562,8 @@ def run_tree(args):
         opts["fresh_per_round"] = args.fresh
     if args.block_threads:
         opts["block_threads"] = args.block_threads
+    if args.grid_blocks:
+        opts["grid_blocks"] = args.grid_blocks
     plan = pip.tree_plan(n, eps, **opts)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
