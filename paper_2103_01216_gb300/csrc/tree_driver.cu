@@ -56,11 +56,11 @@ constexpr unsigned kFullT = 0xffffffffu;
 constexpr uint32_t kMaxSlots = 32;  // items per thread and round (one mark bit each)
 constexpr uint32_t kTreeThreads = 512;
 // A marked leaf's sibling and grandparent, found in phase A, are kept on chip
-// for phase B (slots q < kCacheSlots of each thread, two 32-bit words each;
-// which child word of the grandparent to rewrite is a register bit), so that
-// phase B only writes.  Later slots read their records again.
-constexpr uint32_t kCacheSlots = 8;
-constexpr uint32_t kCacheBytesPerThread = 8u * kCacheSlots;
+// for phase B (slots q < qc of each thread, two 32-bit words each; which
+// child word of the grandparent to rewrite is a register bit), so that phase
+// B only writes.  Later slots read their records again.  qc is the largest of
+// 8, 4, 2, 1 that fits the scratch bound without lowering F.
+constexpr uint32_t kCacheSlotChoices[] = {8u, 4u, 2u, 1u};
 constexpr uint32_t kNil32 = 0xFFFFFFFFu;
 #ifndef PIP_TREE_MIN_BLOCKS
 #define PIP_TREE_MIN_BLOCKS 2
@@ -80,7 +80,7 @@ struct TreeArgs {
   uint64_t timeout_ns;
   uint64_t deadline_ns;
   uint32_t max_rounds;
-  uint32_t qc;  // cached slots per thread (0 or kCacheSlots)
+  uint32_t qc;  // cached slots per thread (0, 1, 2, 4 or 8)
 };
 
 __device__ __forceinline__ uint64_t parent_of(const ulonglong2* h, uint64_t v) { return ldcg(&h[2 * v].x); }
@@ -460,9 +460,9 @@ int tree_blocks_per_sm(uint32_t threads, uint64_t smem) {
 // of 2e8 nodes, against 23.3 ms at 300K and 900K and 24.3 ms at 1.25M).
 constexpr uint64_t kTreeL2BytesPerFresh = 216;
 
-// The list engine's plan, with the phase-B cache when it fits the scratch
-// bound without lowering F (otherwise without it).  Unless the caller fixes
-// F, the default prefix C * n^(1-eps) is also capped at L2 / 216 bytes.
+// The list engine's plan, with the largest phase-B cache that fits the
+// scratch bound without lowering F (or none).  Unless the caller fixes F,
+// the default prefix C * n^(1-eps) is also capped at L2 / 216 bytes.
 pip_status make_tree_plan(uint64_t n, double eps, const pip_options* opt, ListPlan* out) {
   pip_options o{};
   if (opt != nullptr) o = *opt;
@@ -472,11 +472,17 @@ pip_status make_tree_plan(uint64_t n, double eps, const pip_options* opt, ListPl
     const double cap = (double)di.l2_bytes / (double)kTreeL2BytesPerFresh;
     if (want > cap) o.fresh_per_round = (uint32_t)cap;
   }
-  ListPlan plain, cached;
+  ListPlan plain;
   pip_status st = make_list_plan(n, eps, &o, &plain, &tree_blocks_per_sm, 0);
   if (st != PIP_OK) return st;
-  st = make_list_plan(n, eps, &o, &cached, &tree_blocks_per_sm, kCacheBytesPerThread);
-  *out = (st == PIP_OK && cached.F == plain.F) ? cached : plain;
+  *out = plain;
+  for (const uint32_t qc : kCacheSlotChoices) {
+    ListPlan cached;
+    if (make_list_plan(n, eps, &o, &cached, &tree_blocks_per_sm, 8u * qc) == PIP_OK && cached.F == plain.F) {
+      *out = cached;
+      break;
+    }
+  }
   return PIP_OK;
 }
 
