@@ -401,6 +401,35 @@ pip_status pip_shuffle_noalloc(void *A_dev, uint64_t n, pip_dtype dtype, uint64_
  */
 pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed, void *stream);
 
+/*
+ * pip_shuffle_host_stream -- shuffles `count` arrays held in host memory, in
+ * order: array j (n elements of dtype at in_hosts[j]) is copied to the
+ * device, shuffled as pip_shuffle(..., seeds[j], eps) would, and copied back
+ * to out_hosts[j] (which may be in_hosts[j]).  A shuffle touches its whole
+ * array, so its own copies cannot overlap it; array j's copies overlap the
+ * shuffles of arrays j-1 and j+1 instead (two device buffers, separate
+ * streams for copies in, shuffles and copies out, ordered by events; the
+ * shuffles run one at a time).
+ *   in_hosts, out_hosts, seeds: host arrays of length count.  The arrays
+ *              are independent: an input must not be another array's output
+ *              (a copy in may run before an earlier array's copy out).  The copies
+ *              are asynchronous and overlap only for page-locked host memory
+ *              (cudaHostAlloc / cudaHostRegister); pageable memory works
+ *              but serialises.  The host buffers must stay valid until
+ *              `stream` reaches the end of the call.
+ *   dev_buf  : NULL (allocated with cudaMallocAsync on `stream` and freed
+ *              the same way), or caller device memory of at least
+ *              min(count, 2) * round_up(n * elem, 256) bytes, 256-byte aligned.
+ *   stream   : the caller's stream; the work starts after what is queued on
+ *              it and `stream` waits for the last copy back, so pip_check(stream)
+ *              reports completion and any device-side error.
+ * Returns PIP_EINVAL for bad arguments (nothing queued), else the first
+ * failure while queueing (after waiting for whatever was queued).
+ */
+pip_status pip_shuffle_host_stream(const void *const *in_hosts, void *const *out_hosts, const uint64_t *seeds,
+                                   uint32_t count, uint64_t n, pip_dtype dtype, double eps, void *dev_buf,
+                                   uint64_t dev_bytes, void *stream);
+
 /* ------------------------------------------------------------ list contraction */
 
 /* One node of a doubly-linked list (16 bytes): the indices of its neighbours,

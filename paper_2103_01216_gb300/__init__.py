@@ -231,6 +231,9 @@ def lib() -> ctypes.CDLL:
         L.pip_batch_run.restype = i32
         L.pip_shuffle_noalloc.argtypes = [vp, u64, i32, u64, dbl, vp]
         L.pip_shuffle_noalloc.restype = i32
+        L.pip_shuffle_host_stream.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(u64),
+                                              ctypes.c_uint32, u64, i32, dbl, vp, u64, vp]
+        L.pip_shuffle_host_stream.restype = i32
         L.pip_calibrate_swap_floor.argtypes = [vp, u64, i32, u64, vp]
         L.pip_calibrate_swap_floor.restype = i32
         L.pip_serve_create.argtypes = [ctypes.POINTER(vp), u64, i32, ctypes.POINTER(ServeOptions)]
@@ -364,6 +367,33 @@ def shuffle(A, seed: int = 0, eps: float = 0.5, *, H=None, stream=None, aux=None
         st_ptr = stats.data_ptr()
     shuffle_ptr(A.data_ptr(), n, d, seed, eps, H_ptr=h_ptr, options=make_options(**options), aux_ptr=aux_ptr,
                 aux_bytes_=aux_n, stats_ptr=st_ptr, stream=_stream_handle(stream))
+
+
+def shuffle_host_stream(ins, outs, seeds, eps: float = 0.5, *, dev_buf=None, stream=None) -> None:
+    """Shuffle a sequence of host (CPU) tensors: ins[j] is copied to the
+    device, shuffled with seeds[j] and copied back to outs[j] (which may be
+    ins[j]); copies overlap the neighbouring shuffles (asynchronous on
+    ``stream``; pinned tensors overlap, pageable ones serialise).  All tensors
+    have the same shape and dtype (1-D 4- or 8-byte, or 2-D 16-byte rows).
+    ``dev_buf``: optional CUDA uint8 tensor of at least
+    min(len, 2) * round_up(bytes, 256) bytes."""
+    ins, outs, seeds = list(ins), list(outs), [int(x) for x in seeds]
+    if not (len(ins) == len(outs) == len(seeds)):
+        raise ValueError("ins, outs and seeds must have the same length")
+    if not ins:
+        return
+    d = tensor_dtype(ins[0])
+    for t in ins + outs:
+        if t.is_cuda or not t.is_contiguous() or t.shape != ins[0].shape or t.dtype != ins[0].dtype:
+            raise ValueError("every array must be a contiguous host tensor of one shape and dtype")
+    k = len(ins)
+    in_p = (ctypes.c_void_p * k)(*[t.data_ptr() for t in ins])
+    out_p = (ctypes.c_void_p * k)(*[t.data_ptr() for t in outs])
+    sd = (ctypes.c_uint64 * k)(*seeds)
+    buf_ptr, buf_n = (dev_buf.data_ptr(), dev_buf.numel() * dev_buf.element_size()) if dev_buf is not None else (None, 0)
+    rc = lib().pip_shuffle_host_stream(in_p, out_p, sd, k, ins[0].shape[0], d, eps, buf_ptr, buf_n,
+                                       _stream_handle(stream))
+    _raise(rc, "pip_shuffle_host_stream")
 
 
 def check(stream=None) -> None:

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpip_gb300.so")
 
-SOURCES = ["grid_driver.cu", "cta_driver.cu", "pip_api.cu", "planner.cpp", "static_scratch.cu", "serve.cu", "calibrate.cu", "cluster_driver.cu", "list_driver.cu", "tree_driver.cu", "scan.cu"]
+SOURCES = ["grid_driver.cu", "cta_driver.cu", "pip_api.cu", "planner.cpp", "static_scratch.cu", "serve.cu", "calibrate.cu", "cluster_driver.cu", "list_driver.cu", "tree_driver.cu", "scan.cu", "host_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
