@@ -63,6 +63,9 @@ namespace {
 #ifndef PIP_SCAN_LB_PER_LANE
 #define PIP_SCAN_LB_PER_LANE 1
 #endif
+#ifndef PIP_SCAN_POLL_NS
+#define PIP_SCAN_POLL_NS 64
+#endif
 constexpr uint32_t kScanThreads = PIP_SCAN_THREADS;     // scanning threads
 constexpr uint32_t kBlockThreads = kScanThreads + 32u;  // and the look-back warp
 constexpr uint32_t kStages = PIP_SCAN_STAGES;           // tile buffers
@@ -250,7 +253,7 @@ __device__ __forceinline__ T look_back(const ScanDesc* ring, uint64_t t, uint32_
     if (lane == 0) {
       T unused;
       for (uint32_t k = 0; desc_read<T>(ring + (top & (kRing - 1)), (uint64_t)top, &unused) == 0; ++k) {
-        __nanosleep(64);
+        if (PIP_SCAN_POLL_NS > 0) __nanosleep(PIP_SCAN_POLL_NS);
         if ((k & 15u) == 15u) {
           if (ld_relaxed_u32(&ctrl->status) != 0u) {
             bad = 1;

@@ -55,6 +55,15 @@ constexpr uint64_t kNil = PIP_TREE_NIL;
 constexpr unsigned kFullT = 0xffffffffu;
 constexpr uint32_t kMaxSlots = 32;  // items per thread and round (one mark bit each)
 constexpr uint32_t kTreeThreads = 512;
+// Slots of a thread decided together in phase A.  Two (twice the chains of
+// random reads in flight) measured no faster on GB300 than one -- 24.9
+// against 24.4 ms at eps = 0.25, 41.3 against 42.4 ms at eps = 0.5 for a tree
+// of 2e8 nodes -- so the rounds are bound by the rate of random accesses, not
+// by their latency; four spill registers.
+#ifndef PIP_TREE_PHASE_A_WIDTH
+#define PIP_TREE_PHASE_A_WIDTH 1
+#endif
+constexpr uint32_t kPhaseAWidth = PIP_TREE_PHASE_A_WIDTH;
 // A marked leaf's sibling and grandparent, found in phase A, are kept on chip
 // for phase B (slots q < qc of each thread, two 32-bit words each; which
 // child word of the grandparent to rewrite is a register bit), so that phase
@@ -95,64 +104,115 @@ __device__ __forceinline__ void tree_slice(uint32_t f, uint32_t* off, uint32_t* 
   *cnt = min(f, f0 + kf) - f0;
 }
 
-// Phase A for node i: 0 = no work (internal node or root), 1 = rakes this
-// round, 2 = carried; *bad set on a pointer that fails its check.  For a leaf
-// that rakes, *s_out and *g_out are its sibling and grandparent and *g_right
-// tells that the parent is the grandparent's right child.
-__device__ __forceinline__ uint32_t tree_decide(const ulonglong2* h, uint64_t i, uint64_t n, bool* bad,
-                                                uint64_t* s_out, uint64_t* g_out, bool* g_right) {
-  const ulonglong2 me = ldcg(&h[2 * i]);  // (parent, left)
-  if (me.y != kNil || me.x == kNil) return 0u;
-  const uint64_t p = me.x;
-  if (p >= n) {
-    *bad = true;
-    return 0u;
-  }
-  const ulonglong2 P = ldcg(&h[2 * p]);  // (g, left of p)
-  const uint64_t pr = right_of(h, p);
-  const uint64_t g = P.x;
-  const uint64_t s = P.y == i ? pr : (pr == i ? P.y : kNil);
-  if (s >= n || (g != kNil && g >= n)) {
-    *bad = true;
-    return 0u;
-  }
-  // the sibling's and the grandparent's child words, loaded together
-  const uint64_t sl = left_of(h, s);
-  const uint64_t sr = right_of(h, s);
-  uint64_t gl = kNil, gr = kNil;
-  if (g != kNil) {
-    gl = left_of(h, g);
-    gr = right_of(h, g);
-  }
-  bool win = true;
-  uint64_t c0 = kNil, c1 = kNil, u = kNil;
-  if (sl == kNil) {
-    win = s > i;  // the sibling is a leaf
-  } else {
-    if (sl >= n || sr >= n) {
+// Phase A for K nodes i[k] of one thread at once: d[k] = 0 for no work
+// (inactive, an internal node or a root), 1 when the leaf rakes this round,
+// 2 when it is carried; *bad is set on a pointer that fails its check (that
+// node then counts as no work).  For a leaf that rakes, s_out[k] and g_out[k]
+// are its sibling and grandparent and g_right[k] tells that the parent is the
+// grandparent's right child.  The K nodes go through the dependent loads
+// (own record, parent, sibling and grandparent, then the nephews' and
+// uncle's left words) stage by stage, so that a thread keeps K chains of
+// random reads in flight instead of one.
+template <int K>
+__device__ __forceinline__ void tree_decide(const ulonglong2* h, const uint64_t (&i)[K], const bool (&act)[K],
+                                            uint64_t n, bool* bad, uint32_t (&d)[K], uint64_t (&s_out)[K],
+                                            uint64_t (&g_out)[K], bool (&g_right)[K]) {
+  bool live[K];
+  uint64_t p[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    d[k] = 0u;
+    s_out[k] = kNil;
+    g_out[k] = kNil;
+    g_right[k] = false;
+    ulonglong2 me = make_ulonglong2(kNil, kNil);
+    if (act[k]) me = ldcg(&h[2 * i[k]]);  // (parent, left)
+    p[k] = me.x;
+    live[k] = act[k] && me.y == kNil && me.x != kNil;  // a leaf with a parent
+    if (live[k] && p[k] >= n) {
       *bad = true;
-      return 0u;
+      live[k] = false;
     }
-    c0 = sl < i ? sl : kNil;  // nephews that could win
-    c1 = sr < i ? sr : kNil;
   }
-  if (g != kNil) {
-    const uint64_t uu = gl == p ? gr : (gr == p ? gl : kNil);
-    if (uu >= n) {
-      *bad = true;
-      return 0u;
+  ulonglong2 P[K];
+  uint64_t pr[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    P[k] = make_ulonglong2(kNil, kNil);
+    pr[k] = kNil;
+    if (live[k]) {
+      P[k] = ldcg(&h[2 * p[k]]);  // (g, left of p)
+      pr[k] = right_of(h, p[k]);
     }
-    u = uu < i ? uu : kNil;
+  }
+  uint64_t s[K], g[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    g[k] = P[k].x;
+    s[k] = P[k].y == i[k] ? pr[k] : (pr[k] == i[k] ? P[k].y : kNil);
+    if (live[k] && (s[k] >= n || (g[k] != kNil && g[k] >= n))) {
+      *bad = true;
+      live[k] = false;
+    }
+  }
+  // the siblings' and the grandparents' child words, loaded together
+  uint64_t sl[K], sr[K], gl[K], gr[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    sl[k] = sr[k] = gl[k] = gr[k] = kNil;
+    if (live[k]) {
+      sl[k] = left_of(h, s[k]);
+      sr[k] = right_of(h, s[k]);
+      if (g[k] != kNil) {
+        gl[k] = left_of(h, g[k]);
+        gr[k] = right_of(h, g[k]);
+      }
+    }
+  }
+  bool win[K];
+  uint64_t c0[K], c1[K], u[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    win[k] = true;
+    c0[k] = c1[k] = u[k] = kNil;
+    if (!live[k]) continue;
+    if (sl[k] == kNil) {
+      win[k] = s[k] > i[k];  // the sibling is a leaf
+    } else {
+      if (sl[k] >= n || sr[k] >= n) {
+        *bad = true;
+        live[k] = false;
+        continue;
+      }
+      c0[k] = sl[k] < i[k] ? sl[k] : kNil;  // nephews that could win
+      c1[k] = sr[k] < i[k] ? sr[k] : kNil;
+    }
+    if (g[k] != kNil) {
+      const uint64_t uu = gl[k] == p[k] ? gr[k] : (gr[k] == p[k] ? gl[k] : kNil);
+      if (uu >= n) {
+        *bad = true;
+        live[k] = false;
+        continue;
+      }
+      u[k] = uu < i[k] ? uu : kNil;
+    }
   }
   // a smaller nephew or uncle beats i only if it is a leaf
-  const bool l0 = c0 != kNil && left_of(h, c0) == kNil;
-  const bool l1 = c1 != kNil && left_of(h, c1) == kNil;
-  const bool lu = u != kNil && left_of(h, u) == kNil;
-  win = win && !l0 && !l1 && !lu;
-  *s_out = s;
-  *g_out = g;
-  *g_right = g != kNil && gr == p;
-  return win ? 1u : 2u;
+  bool l0[K], l1[K], lu[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    l0[k] = live[k] && c0[k] != kNil && left_of(h, c0[k]) == kNil;
+    l1[k] = live[k] && c1[k] != kNil && left_of(h, c1[k]) == kNil;
+    lu[k] = live[k] && u[k] != kNil && left_of(h, u[k]) == kNil;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!live[k]) continue;
+    d[k] = (win[k] && !l0[k] && !l1[k] && !lu[k]) ? 1u : 2u;
+    s_out[k] = s[k];
+    g_out[k] = g[k];
+    g_right[k] = g[k] != kNil && gr[k] == p[k];
+  }
 }
 
 // Phase B for a marked leaf i in round r (0-based).  Every pointer it
@@ -247,52 +307,68 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
     if (nslot > kMaxSlots && threadIdx.x == 0) fail(PIP_EINTERNAL);  // the planner keeps this from happening
 
     // ---- phase A: mark the leaves that rake, keep the others
+    // (kPhaseAWidth slots of a thread at a time)
     uint32_t marks = 0, rights = 0;
-    for (uint32_t q = 0; q < nslot && q < kMaxSlots; ++q) {
-      uint32_t i = 0;
-      bool act;
+    const uint32_t nq = min(nslot, kMaxSlots);
+    auto slot_item = [&](uint32_t q, uint32_t* i_out) -> bool {
+      if (q >= nq) return false;
       if (q < nfs) {
         const uint32_t o = q * NT + threadIdx.x;
-        act = o < nf;
-        i = fbase + o;
-      } else {
-        const uint32_t pq = (q - nfs) * NT + threadIdx.x;
-        act = pq < nlg;
-        if (act) i = (pq < nloc) ? loc_in[pq] : ldcg(Qg + pq);
+        *i_out = fbase + o;
+        return o < nf;
       }
-      uint32_t d = 0;
-      if (act) {
-        bool bad = false, g_right = false;
-        uint64_t sib = kNil, gp = kNil;
-        d = tree_decide(h, i, a.n, &bad, &sib, &gp, &g_right);
-        if (bad) fail(PIP_EINVAL);
-        if (d == 1u && q < a.qc) {
-          c_sib[q * NT + threadIdx.x] = (uint32_t)sib;
-          c_gp[q * NT + threadIdx.x] = gp == kNil ? kNil32 : (uint32_t)gp;
-          if (g_right) rights |= 1u << q;
+      const uint32_t pq = (q - nfs) * NT + threadIdx.x;
+      if (pq >= nlg) return false;
+      *i_out = (pq < nloc) ? loc_in[pq] : ldcg(Qg + pq);
+      return true;
+    };
+    for (uint32_t q0 = 0; q0 < nq; q0 += kPhaseAWidth) {
+      uint64_t iv[kPhaseAWidth];
+      bool act[kPhaseAWidth];
+      uint32_t d[kPhaseAWidth];
+      uint64_t sib[kPhaseAWidth], gp[kPhaseAWidth];
+      bool g_right[kPhaseAWidth];
+#pragma unroll
+      for (uint32_t k = 0; k < kPhaseAWidth; ++k) {
+        uint32_t ii = 0;
+        act[k] = slot_item(q0 + k, &ii);
+        iv[k] = ii;
+      }
+      bool bad = false;
+      tree_decide<(int)kPhaseAWidth>(h, iv, act, a.n, &bad, d, sib, gp, g_right);
+      if (bad) fail(PIP_EINVAL);
+#pragma unroll
+      for (uint32_t k = 0; k < kPhaseAWidth; ++k) {
+        const uint32_t q = q0 + k;
+        if (q >= nq) break;  // uniform: nq is the same for the whole block
+        if (d[k] == 1u && q < a.qc) {
+          c_sib[q * NT + threadIdx.x] = (uint32_t)sib[k];
+          c_gp[q * NT + threadIdx.x] = gp[k] == kNil ? kNil32 : (uint32_t)gp[k];
+          if (g_right[k]) rights |= 1u << q;
         }
-      }
-      if (d == 1u) marks |= 1u << q;
-      const bool keep = d == 2u;
-      const unsigned mask = __ballot_sync(kFullT, keep);
-      if (mask) {
-        const int leader = __ffs(mask) - 1;
-        uint32_t wbase = 0;
-        if ((int)lane == leader) wbase = atomicAdd(&s_lcount, (uint32_t)__popc(mask));
-        wbase = __shfl_sync(kFullT, wbase, leader);
-        const uint32_t idx = wbase + __popc(mask & ((1u << lane) - 1u));
-        const bool spill = keep && idx >= a.kloc;
-        if (keep && !spill) loc_out[idx] = i;
-        const unsigned smask = __ballot_sync(kFullT, spill);
-        if (smask) {
-          const int sl = __ffs(smask) - 1;
-          uint32_t qbase = 0;
-          if ((int)lane == sl) qbase = atomicAdd(cnt_out, (uint32_t)__popc(smask));
-          qbase = __shfl_sync(kFullT, qbase, sl);
-          if (spill) {
-            const uint32_t qq = qbase + __popc(smask & ((1u << lane) - 1u));
-            if (qq < a.kmax) stcg(Qout + qq, i);
-            else fail(PIP_EINTERNAL);  // cannot happen: the throttle bounds the carried leaves by kmax
+        if (d[k] == 1u) marks |= 1u << q;
+        const uint32_t i = (uint32_t)iv[k];
+        const bool keep = d[k] == 2u;
+        const unsigned mask = __ballot_sync(kFullT, keep);
+        if (mask) {
+          const int leader = __ffs(mask) - 1;
+          uint32_t wbase = 0;
+          if ((int)lane == leader) wbase = atomicAdd(&s_lcount, (uint32_t)__popc(mask));
+          wbase = __shfl_sync(kFullT, wbase, leader);
+          const uint32_t idx = wbase + __popc(mask & ((1u << lane) - 1u));
+          const bool spill = keep && idx >= a.kloc;
+          if (keep && !spill) loc_out[idx] = i;
+          const unsigned smask = __ballot_sync(kFullT, spill);
+          if (smask) {
+            const int sl = __ffs(smask) - 1;
+            uint32_t qbase = 0;
+            if ((int)lane == sl) qbase = atomicAdd(cnt_out, (uint32_t)__popc(smask));
+            qbase = __shfl_sync(kFullT, qbase, sl);
+            if (spill) {
+              const uint32_t qq = qbase + __popc(smask & ((1u << lane) - 1u));
+              if (qq < a.kmax) stcg(Qout + qq, i);
+              else fail(PIP_EINTERNAL);  // cannot happen: the throttle bounds the carried leaves by kmax
+            }
           }
         }
       }
