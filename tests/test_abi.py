@@ -130,3 +130,41 @@ def test_batch_plan_host_only(pip):
     assert plan.smem_bytes + 256 <= pip.AUX_C * x + 4096
     items[1].n = 1 << 32
     assert pip.lib().pip_batch_plan_make(items, 3, pip.U32, 0.5, None, ctypes.byref(plan)) == pip.PIP_EINVAL
+
+
+def test_host_stream_tree_and_scan_argument_errors(pip):
+    L = pip.lib()
+    vp = ctypes.c_void_p
+    one = (vp * 1)(vp(4096))
+    seeds = (ctypes.c_uint64 * 1)(1)
+    # nothing to do, or nothing touched: no GPU needed
+    assert L.pip_shuffle_host_stream(None, None, None, 0, 10, pip.U64, 0.5, None, 0, None) == pip.PIP_OK
+    assert L.pip_shuffle_host_stream(one, one, seeds, 1, 0, pip.U64, 0.5, None, 0, None) == pip.PIP_OK
+    assert L.pip_shuffle_host_stream(None, one, seeds, 1, 10, pip.U64, 0.5, None, 0, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle_host_stream(one, one, None, 1, 10, pip.U64, 0.5, None, 0, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle_host_stream(one, one, seeds, 1, 10, 9, 0.5, None, 0, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle_host_stream(one, one, seeds, 1, 10, pip.U64, 1.0, None, 0, None) == pip.PIP_EINVAL
+    nul = (vp * 1)(None)
+    assert L.pip_shuffle_host_stream(nul, one, seeds, 1, 10, pip.U64, 0.5, None, 0, None) == pip.PIP_EINVAL
+    # tree contraction: eps, size and alignment checks come first; n <= 1 is a no-op
+    assert L.pip_tree_contract(vp(4096), 10, 0.0, None) == pip.PIP_EINVAL
+    assert L.pip_tree_contract(vp(4096), 1 << 32, 0.5, None) == pip.PIP_EINVAL
+    assert L.pip_tree_contract(vp(4096 + 16), 10, 0.5, None) == pip.PIP_EINVAL  # records need 32-byte alignment
+    assert L.pip_tree_contract(None, 10, 0.5, None) == pip.PIP_EINVAL
+    assert L.pip_tree_contract(None, 1, 0.5, None) == pip.PIP_OK
+    # scan: dtype and alignment
+    assert L.pip_scan(vp(4096), 10, pip.REC128, None, None) == pip.PIP_EINVAL
+    assert L.pip_scan(vp(4096 + 8), 10, pip.U64, None, None) == pip.PIP_EINVAL
+    assert L.pip_scan(None, 0, pip.U32, None, None) == pip.PIP_OK
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.25, 0.5, 0.75])
+@pytest.mark.parametrize("n", [3, 1000, 1 << 20, 2 * 10**8 - 1, (1 << 32) - 3])
+def test_list_and_tree_plans_obey_the_aux_bound(pip, eps, n):
+    for plan in (pip.list_plan(n, eps), pip.tree_plan(n, eps)):
+        F = plan["fresh_per_round"]
+        assert 1 <= F <= n
+        assert plan["max_active"] == F * 5 // 2 + 2
+        assert plan["aux_bytes"] + plan["smem_bytes"] <= plan["aux_bound_bytes"]
+        assert plan["aux_bound_bytes"] == int(128 * n ** (1 - eps)) + 4096
+    assert pip.tree_plan(n, eps)["elem_bytes"] == 32 and pip.tree_plan(n, eps)["driver"] == pip.DRIVER_TREE
