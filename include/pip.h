@@ -407,7 +407,7 @@ pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, ui
  * device, shuffled as pip_shuffle(..., seeds[j], eps) would, and copied back
  * to out_hosts[j] (which may be in_hosts[j]).  A shuffle touches its whole
  * array, so its own copies cannot overlap it; array j's copies overlap the
- * shuffles of arrays j-1 and j+1 instead (two device buffers, separate
+ * shuffles of arrays j-1 and j+1 instead (three device buffers, separate
  * streams for copies in, shuffles and copies out, ordered by events; the
  * shuffles run one at a time).
  *   in_hosts, out_hosts, seeds: host arrays of length count.  The arrays
@@ -419,7 +419,7 @@ pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, ui
  *              `stream` reaches the end of the call.
  *   dev_buf  : NULL (allocated with cudaMallocAsync on `stream` and freed
  *              the same way), or caller device memory of at least
- *              min(count, 2) * round_up(n * elem, 256) bytes, 256-byte aligned.
+ *              min(count, 3) * round_up(n * elem, 256) bytes, 256-byte aligned.
  *   stream   : the caller's stream; the work starts after what is queued on
  *              it and `stream` waits for the last copy back, so pip_check(stream)
  *              reports completion and any device-side error.

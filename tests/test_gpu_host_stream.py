@@ -65,6 +65,14 @@ def test_single_array_and_caller_buffer(pip):
     with pytest.raises(pip.PipError) as e:
         pip.shuffle_host_stream([t, t2], [t, t2], [1, 2], eps=0.25, dev_buf=buf)
     assert e.value.code == pip.PIP_EINVAL
+    # five arrays go round three caller buffers
+    slot = ((n * 8 + 255) // 256) * 256
+    buf3 = torch.empty(3 * slot, dtype=torch.uint8, device="cuda")
+    ts = [host_tensor(torch, a, True) for _ in range(5)]
+    pip.shuffle_host_stream(ts, ts, [20, 21, 22, 23, 24], eps=0.25, dev_buf=buf3)
+    pip.check()
+    for j, tj in enumerate(ts):
+        assert np.array_equal(to_np(tj, a), expected(a, 20 + j)), j
 
 
 def test_larger_arrays_many_steps(pip):
