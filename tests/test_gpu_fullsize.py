@@ -10,6 +10,9 @@ configuration ``bench.py`` times (default plans).
   array against the oracle, computed by a process pool started with ``spawn``.
 * scratch: with caller-provided scratch of exactly the planned size the
   device's free memory does not move, and the plan obeys the aux bound.
+* tree contraction of 2^25 leaves and list contraction of 2^26 nodes at
+  their default plans (the tree's has the bench launch's shape), and the scan
+  of 10^9 uint32 values (the bench's size): whole outputs against the oracle.
 """
 import multiprocessing as mp
 import os
@@ -148,3 +151,58 @@ def test_scratch_is_exactly_the_plan(pip, eps):
     seen = torch.zeros(n, dtype=torch.bool, device="cuda")
     seen[A] = True
     assert bool(seen.all())
+
+
+def test_tree_contraction_in_the_bench_launch_shape(pip):
+    # 2^25 leaves (6.7e7 nodes, 2 GB): the default plan at eps = 0.25 has
+    # the bench launch's shape (L2-sized prefix, 304 blocks, phase-B cache);
+    # the whole output against the oracle's schedule, and every rake undone
+    torch = torch_cuda()
+    rec = workloads.random_tree(1 << 25, rng_seed=25)
+    n = rec.shape[0]
+    plan = pip.tree_plan(n, 0.25)
+    F = plan["fresh_per_round"]
+    assert plan["max_active"] == F * 5 // 2 + 2
+    t = torch.from_numpy(rec.view(np.int64)).cuda()
+    pip.tree_contract(t, eps=0.25)
+    pip.check()
+    out = t.cpu().numpy().view(np.uint64).reshape(rec.shape)
+    del t
+    torch.cuda.empty_cache()
+    want = rec.copy()
+    oracle.tree_contract(want, F, F * 5 // 2 + 2)
+    assert np.array_equal(out, want)
+    rc, back = oracle.tree_uncontract(out, rec)
+    assert rc == 0 and np.array_equal(back, rec)
+
+
+def test_list_contraction_one_long_list(pip):
+    # one random list of 2^26 nodes at the default plan (eps = 0.25)
+    torch = torch_cuda()
+    rec = workloads.random_lists(1 << 26, rng_seed=26)
+    t = torch.from_numpy(rec.view(np.int64)).cuda()
+    pip.list_contract(t, eps=0.25)
+    pip.check()
+    out = t.cpu().numpy().view(np.uint64).reshape(rec.shape)
+    del t
+    torch.cuda.empty_cache()
+    assert np.array_equal(out, oracle.list_contract(rec.copy()))
+
+
+def test_scan_1e9_u32(pip):
+    # the bench's scan size: 10^9 uint32 values below 2^20, whole output and
+    # total against the oracle's up-sweep / down-sweep
+    torch = torch_cuda()
+    n = 10**9
+    a = np.random.default_rng(9).integers(0, 1 << 20, size=n, dtype=np.uint32)
+    t = torch.from_numpy(a.view(np.int32)).cuda()
+    tot = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pip.scan(t, total=tot)
+    pip.check()
+    got = t.cpu().numpy().view(np.uint32)
+    got_tot = int(tot.cpu().numpy().view(np.uint32)[0])
+    del t
+    torch.cuda.empty_cache()
+    want_tot = oracle.scan_exclusive(a)  # in place on the host copy
+    assert got_tot == want_tot
+    assert np.array_equal(got, a)
