@@ -96,7 +96,7 @@ static_assert(sizeof(ScanCtrl) == 256, "scan control block is 256 bytes");
 constexpr uint32_t kTagBits = 24;
 constexpr uint64_t kTagMask = (1ull << kTagBits) - 1ull;
 
-struct ScanDesc {
+struct __align__(16) ScanDesc {
   unsigned long long w[2];
 };
 
@@ -121,10 +121,27 @@ __device__ __forceinline__ void desc_publish(ScanDesc* d, uint64_t tile, uint64_
 
 // 0 when the descriptor does not (yet) describe `tile`; else its flag, with
 // the value in *value.
-template <typename T>
+// A window read takes each descriptor with one 16-byte load at L2
+// (kStrong = false): it may tear between the two words or return an older
+// state of a word, but a torn pair fails the tag / flag check and is read
+// again, and an older state is the tile's sum where its prefix is already
+// out -- still a correct value, the walk just goes further back.  The
+// single-lane poll of one descriptor (kStrong = true) uses relaxed loads,
+// which the compiler may not hoist out of the polling loop.
+#ifndef PIP_SCAN_DESC_V2
+#define PIP_SCAN_DESC_V2 1
+#endif
+template <typename T, bool kStrong = false>
 __device__ __forceinline__ uint64_t desc_read(const ScanDesc* d, uint64_t tile, T* value) {
-  const unsigned long long a = ld_relaxed_u64(&d->w[0]);
-  const unsigned long long b = ld_relaxed_u64(&d->w[1]);
+  unsigned long long a, b;
+  if (PIP_SCAN_DESC_V2 && !kStrong) {
+    const ulonglong2 ab = __ldcg(reinterpret_cast<const ulonglong2*>(d));
+    a = ab.x;
+    b = ab.y;
+  } else {
+    a = ld_relaxed_u64(&d->w[0]);
+    b = ld_relaxed_u64(&d->w[1]);
+  }
   const uint64_t tag = tile & kTagMask;
   if ((a >> 40) != tag || (b >> 40) != tag) return 0;
   const uint64_t fa = (a >> 38) & 3ull, fb = (b >> 38) & 3ull;
@@ -252,7 +269,7 @@ __device__ __forceinline__ T look_back(const ScanDesc* ring, uint64_t t, uint32_
     uint32_t bad = 0;
     if (lane == 0) {
       T unused;
-      for (uint32_t k = 0; desc_read<T>(ring + (top & (kRing - 1)), (uint64_t)top, &unused) == 0; ++k) {
+      for (uint32_t k = 0; desc_read<T, true>(ring + (top & (kRing - 1)), (uint64_t)top, &unused) == 0; ++k) {
         if (PIP_SCAN_POLL_NS > 0) __nanosleep(PIP_SCAN_POLL_NS);
         if ((k & 15u) == 15u) {
           if (ld_relaxed_u32(&ctrl->status) != 0u) {
