@@ -5,31 +5,30 @@
 // The GPU design is a single pass over the array in tiles with decoupled
 // look-back: block b of a grid of G resident blocks takes tiles b, b + G,
 // ..., each moved into shared memory by a bulk asynchronous copy
-// (cp.async.bulk completing on an mbarrier) into a ring of kStages tile
-// buffers, kStages - 2 copies ahead of the tile being scanned.  The block is
-// warp-specialised:
-//   - the scanning warps scan tile i in shared memory (each thread a run of
-//     consecutive elements, then the warps), publish the tile's sum in a
-//     descriptor, hand it to the look-back warp and, one tile behind, add
-//     the prefix the look-back warp found for tile i - 1 and send that tile
-//     back with a bulk copy from shared memory;
-//   - the look-back warp derives the sum of everything before tile i from
-//     its predecessors' descriptors (the look-back, 32 * kLbPerLane
-//     descriptors per L2 round trip) and publishes the inclusive prefix,
-//     while the scanning warps work on the next tile.
-// So the look-back's latency overlaps the data path instead of stalling it,
-// and each element is read once and written once: the pass is bound by HBM
-// bandwidth.
+// (cp.async.bulk completing on an mbarrier), two or three copies ahead.  The
+// block is warp-specialised:
+//   - the scanning warps read tile i into registers (which frees its
+//     buffer), scan it, publish its sum in a descriptor and hand the sum to
+//     the look-back warp through an mbarrier; kDefer tiles later they add
+//     the prefix the look-back warp handed back, write the tile to a staging
+//     buffer and send it out with a bulk copy;
+//   - the look-back warp derives each tile's exclusive prefix from its
+//     predecessors' descriptors (32 per L2 round trip) and publishes the
+//     inclusive prefix.
+// The two roles meet only at the mbarriers of one tile, so a look-back can
+// take kDefer tiles' time before the scanning warps wait for it, and each
+// element is read once and written once: the pass is bound by HBM bandwidth.
 //
 // The descriptors form a ring of kRing entries reused modulo kRing, tagged
-// with the tile index.  A block publishes the sum of a tile only after the
-// look-back of its tile two places earlier has ended, and a look-back never
-// reads further back than the tile G places earlier (whose prefix its block
-// published before it started), so the tiles whose descriptors are read or
-// written at one time span fewer than 6 G indices; a ring of 8 G or more is
-// never overwritten while it is read.  The auxiliary space is therefore a
-// constant (the ring and a control block, 64 KB), whatever n -- the space
-// bound of the paper's strong PIP algorithm.
+// with the tile index.  A block publishes the sum of its local tile i only
+// after the look-back of its tile i - 1 - kDefer has ended, and a look-back
+// never reads further back than its block's previous tile (whose prefix was
+// published before it started).  While one look-back waits, no block can get
+// more than (kDefer + 1) G tiles past its first missing sum, so the indices
+// read or written at one time span fewer than (2 kDefer + 3) G; a ring of
+// (2 kDefer + 4) G or more is never overwritten while it is read.  The
+// auxiliary space is therefore a constant (the ring and a control block,
+// 64 KB), whatever n -- the space bound of the paper's strong PIP algorithm.
 //
 // Addition is modulo 2^w (w = 32 or 64), which is associative, so the result
 // does not depend on the order in which partial sums are combined: the
@@ -45,20 +44,38 @@
 namespace pip {
 namespace {
 
-// Shape: kStages tile buffers of PIP_SCAN_TILE_KB each (one block per SM),
-// PIP_SCAN_THREADS scanning threads plus the look-back warp.  Four 56 KB
-// buffers (two copies ahead) and 512 scanning threads measured best on GB300
-// at 10^9 elements: 75 % (u64) and 81 % (u32) of the HBM copy bandwidth,
-// against 74-77 % for 48 KB, 71 % for 40 KB x 5, 54-57 % for 32 KB x 6,
-// 53-54 % for 64 KB x 3 (one copy ahead) and 60-65 % for 768 threads.
+// Shape (one block per SM): PIP_SCAN_THREADS scanning threads plus the
+// look-back warp; per element size a tile size and a number of tile buffers
+// (all but one for loads, one staging tile for the stores), and the
+// deferral: tiles between a tile's scan and its finish.  Measured on GB300
+// at 10^9 elements (fraction of the HBM copy bandwidth, u64 / u32):
+//   40 KB x 5, deferral 2: 86 / 87 %   48 KB x 4, deferral 2: 82 / 89 %
+//   56 KB x 4, deferral 1: 85 / 84 %   56 KB x 4, deferral 2: 81 / 85 %
+//   48 KB x 4, deferral 1: 78 / 81 %   32 KB x 6, deferral 2: 62 / 66 %
+// (two deferred tiles of 56 KB spill registers at u64; 512 scanning threads
+// keep a thread's 16-byte shared-memory accesses free of bank conflicts).
 #ifndef PIP_SCAN_THREADS
 #define PIP_SCAN_THREADS 512
 #endif
-#ifndef PIP_SCAN_TILE_KB
-#define PIP_SCAN_TILE_KB 56
+#ifdef PIP_SCAN_TILE_KB
+#define PIP_SCAN_TILE_KB_4 PIP_SCAN_TILE_KB
+#define PIP_SCAN_TILE_KB_8 PIP_SCAN_TILE_KB
 #endif
-#ifndef PIP_SCAN_STAGES
-#define PIP_SCAN_STAGES 4
+#ifdef PIP_SCAN_STAGES
+#define PIP_SCAN_STAGES_4 PIP_SCAN_STAGES
+#define PIP_SCAN_STAGES_8 PIP_SCAN_STAGES
+#endif
+#ifndef PIP_SCAN_TILE_KB_4
+#define PIP_SCAN_TILE_KB_4 48
+#endif
+#ifndef PIP_SCAN_STAGES_4
+#define PIP_SCAN_STAGES_4 4
+#endif
+#ifndef PIP_SCAN_TILE_KB_8
+#define PIP_SCAN_TILE_KB_8 40
+#endif
+#ifndef PIP_SCAN_STAGES_8
+#define PIP_SCAN_STAGES_8 5
 #endif
 #ifndef PIP_SCAN_LB_PER_LANE
 #define PIP_SCAN_LB_PER_LANE 1
@@ -68,15 +85,28 @@ namespace {
 #endif
 constexpr uint32_t kScanThreads = PIP_SCAN_THREADS;     // scanning threads
 constexpr uint32_t kBlockThreads = kScanThreads + 32u;  // and the look-back warp
-constexpr uint32_t kStages = PIP_SCAN_STAGES;           // tile buffers
-constexpr uint32_t kAhead = kStages - 2u;               // copies in flight ahead
-constexpr uint32_t kTileBytes = PIP_SCAN_TILE_KB * 1024;
-constexpr uint32_t kSmemBytes = kStages * kTileBytes;  // dynamic shared memory
+#ifndef PIP_SCAN_DEFER
+#define PIP_SCAN_DEFER 2
+#endif
+constexpr uint32_t kDefer = PIP_SCAN_DEFER;  // tiles between a tile's scan and its finish
+constexpr uint32_t kSlots = 4;               // hand-over slots between the two warp roles
 constexpr uint32_t kLbPerLane = PIP_SCAN_LB_PER_LANE;
+
+// The tile shape of one element type.
+template <typename T>
+struct ScanShape {
+  static constexpr uint32_t kTileBytes = (sizeof(T) == 4 ? PIP_SCAN_TILE_KB_4 : PIP_SCAN_TILE_KB_8) * 1024u;
+  static constexpr uint32_t kStages = sizeof(T) == 4 ? PIP_SCAN_STAGES_4 : PIP_SCAN_STAGES_8;  // tile buffers
+  static constexpr uint32_t kLoadBufs = kStages - 1u;  // tiles loading or being read
+  static constexpr uint32_t kAhead = kLoadBufs - 1u;   // copies in flight ahead
+  static constexpr uint32_t kSmemBytes = kStages * kTileBytes;
+  static_assert(kStages >= 3, "at least one copy ahead");
+};
 constexpr uint32_t kRing = 4096;  // descriptors, a power of two
 constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
-constexpr uint32_t kBarScan = 1, kBarHandoff = 2;  // named barriers
-static_assert(kStages >= 3 && kScanThreads % 32u == 0 && kBlockThreads <= 1024u, "scan shape");
+constexpr uint32_t kBarScan = 1;  // named barrier of the scanning threads
+static_assert(kScanThreads % 32u == 0 && kBlockThreads <= 1024u, "scan shape");
+static_assert(kDefer >= 1 && kSlots >= kDefer + 2, "hand-over slots outlast the deferral");
 
 struct ScanCtrl {
   unsigned long long unused;
@@ -298,51 +328,78 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// mbarrier arrive (one arrival; the phase completes with it).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // One pass over tiles of kItems elements, kPer consecutive elements per
 // scanning thread.  Block b takes its m tiles b, b + G, ... (G = grid size,
-// every block resident); its local tile i sits in buffer i % kStages.  Per
-// local tile i the scanning threads
-//   issue the copy of tile i + kAhead (into the buffer of tile i - 2, once
-//   that tile's store has read it), wait for tile i, scan it into registers,
-//   publish its sum,                                       -- then handoff H(i)
-//   finish tile i - 1: add the prefix the look-back warp found for it, write
-//   it to its buffer and store it,
-// and the look-back warp, between H(i) and H(i + 1), finds tile i's prefix.
-// A failed wait (status set) never changes which copies are issued or
-// awaited; it only turns later look-backs into no-ops (the output is then
-// unspecified), so the block always drains its copies before it exits.
+// every block resident).  Local tile i arrives in load buffer i % kLoadBufs
+// (kAhead copies ahead); the scanning threads read it into registers (which
+// frees the buffer), scan it, publish its sum and hand the sum to the
+// look-back warp (mbarrier agg[i % kSlots]).  Tile i is finished kDefer tiles
+// later, once the look-back warp has handed back its prefix (mbarrier
+// pre[i % kSlots]): the prefix is added to the values still held in
+// registers, written to the staging buffer and stored with a bulk copy.  So a
+// tile's look-back may take up to kDefer tiles' time before the scanning
+// threads wait for it.  Every wait is bounded; a failed one changes no
+// arrival and no copy (the output is then unspecified), so no wait on the
+// other side runs into its own limit because of it.
 template <typename T>
 __global__ void __launch_bounds__(kBlockThreads, 1)
     scan_kernel(T* A, uint64_t n, T* total_out, ScanCtrl* ctrl, ScanDesc* ring, uint64_t timeout_ns,
                 uint32_t* latch) {
+  constexpr uint32_t kTileBytes = ScanShape<T>::kTileBytes;
+  constexpr uint32_t kLoadBufs = ScanShape<T>::kLoadBufs;
+  constexpr uint32_t kAhead = ScanShape<T>::kAhead;
   constexpr uint32_t kItems = kTileBytes / sizeof(T);
   constexpr uint32_t kPer = kItems / kScanThreads;
   constexpr uint32_t kVec = 16u / sizeof(T);  // elements per 16-byte access
   static_assert(kPer * kScanThreads == kItems && kPer % kVec == 0, "tile shape");
   extern __shared__ __align__(128) unsigned char s_raw[];
-  T* const s_buf = reinterpret_cast<T*>(s_raw);  // kStages tiles of kItems
-  __shared__ __align__(8) uint64_t s_bar[kStages];
+  T* const s_load = reinterpret_cast<T*>(s_raw);   // kLoadBufs tiles
+  T* const s_stage = s_load + kLoadBufs * kItems;  // one tile, source of the bulk stores
+  __shared__ __align__(8) uint64_t s_bar_load[kLoadBufs];
+  __shared__ __align__(8) uint64_t s_bar_agg[kSlots];
+  __shared__ __align__(8) uint64_t s_bar_pre[kSlots];
   __shared__ T s_warp[kScanThreads / 32u];
-  __shared__ T s_agg[2];  // tile sums, scanning threads -> look-back warp
-  __shared__ T s_pre[2];  // tile prefixes, look-back warp -> scanning threads
+  __shared__ T s_agg[kSlots];  // tile sums, scanning threads -> look-back warp
+  __shared__ T s_pre[kSlots];  // tile prefixes, look-back warp -> scanning threads
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint64_t ntiles = (n + kItems - 1) / kItems;
   const uint64_t G = gridDim.x, blk = blockIdx.x;
   const uint64_t m = blk < ntiles ? (ntiles - 1 - blk) / G + 1 : 0;  // this block's tiles
   if (tid == 0) {
-    for (uint32_t q = 0; q < kStages; ++q) mbar_init(&s_bar[q], 1);
+    for (uint32_t q = 0; q < kLoadBufs; ++q) mbar_init(&s_bar_load[q], 1);
+    for (uint32_t q = 0; q < kSlots; ++q) {
+      mbar_init(&s_bar_agg[q], 1);
+      mbar_init(&s_bar_pre[q], 1);
+    }
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
 
   if (warp == kScanThreads / 32u) {
-    // ---- the look-back warp
+    // ---- the look-back warp: tile i's sum in, tile i's prefix out
     bool failed = false;
-    for (uint64_t i = 0;; ++i) {
-      named_sync(kBarHandoff, kBlockThreads);  // H(i)
-      if (i >= m) break;
+    for (uint64_t i = 0; i < m; ++i) {
+      const uint32_t slot = (uint32_t)(i % kSlots), par = (uint32_t)((i / kSlots) & 1u);
+      // lane 0 waits for the sum (the arrive releases it, the wait acquires
+      // it) and hands it to the other lanes
+      uint32_t ok = 1;
+      T agg = 0;
+      if (lane == 0) {
+        ok = mbar_wait(&s_bar_agg[slot], par, timeout_ns) ? 1u : 0u;
+        agg = s_agg[slot];
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      agg = __shfl_sync(0xffffffffu, agg, 0);
+      if (!ok) {
+        if (lane == 0) set_status(&ctrl->status, PIP_ETIMEOUT);
+        failed = true;
+      }
       const uint64_t t = blk + i * G;
-      const T agg = s_agg[i & 1u];
       T prefix = 0;
       if (t > 0 && !failed) {
         uint32_t fail = 0;
@@ -351,9 +408,11 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         if (!failed && lane == 0) desc_publish<T>(ring + (t & (kRing - 1)), t, kFlagPrefix, (T)(prefix + agg));
       }
       if (lane == 0) {
-        s_pre[i & 1u] = prefix;
+        s_pre[slot] = prefix;
         if (t == ntiles - 1 && total_out != nullptr) stcg(total_out, (T)(prefix + agg));
+        mbar_arrive(&s_bar_pre[slot]);
       }
+      __syncwarp();
     }
     return;
   }
@@ -364,40 +423,52 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
   auto start_load = [&](uint64_t i) {
     const uint64_t u = blk + i * G;
     if (i < m && full_tile(u)) {
-      uint64_t* bar = &s_bar[i % kStages];
+      uint64_t* bar = &s_bar_load[i % kLoadBufs];
       mbar_expect_tx(bar, kTileBytes);
-      bulk_load(s_buf + (i % kStages) * kItems, A + u * kItems, kTileBytes, bar);
+      bulk_load(s_load + (i % kLoadBufs) * kItems, A + u * kItems, kTileBytes, bar);
     }
   };
   if (tid == 0)
     for (uint32_t i = 0; i < kAhead; ++i) start_load(i);
-  T vprev[kPer];
-  T offprev = 0;
-  uint64_t tprev = 0;
-  for (uint64_t i = 0; i <= m; ++i) {
-    T vcur[kPer];
-    T offcur = 0;
-    const uint64_t t = blk + i * G;
+  // values of the tiles waiting for their prefix: vd[0] the newest
+  T vd[kDefer + 1][kPer];
+  T offd[kDefer + 1];
+  uint64_t td[kDefer + 1];
+#pragma unroll
+  for (uint32_t d = 0; d <= kDefer; ++d) {
+    offd[d] = 0;
+    td[d] = 0;
+  }
+  for (uint64_t i = 0; i < m + kDefer; ++i) {
+    // the staging buffer's last bulk store has read it (it is written below,
+    // after a barrier of the scanning threads)
+    if (tid == 0) bulk_wait_read();
+    // shift the pending tiles: slot 0 takes tile i, slot kDefer is finished now
+#pragma unroll
+    for (uint32_t d = kDefer; d >= 1; --d) {
+#pragma unroll
+      for (uint32_t k = 0; k < kPer; ++k) vd[d][k] = vd[d - 1][k];
+      offd[d] = offd[d - 1];
+      td[d] = td[d - 1];
+    }
     if (i < m) {
-      // the buffer of tile i + kAhead last held tile i - 2, stored at the
-      // end of the previous step
-      if (tid == 0) {
-        bulk_wait_read();
-        start_load(i + kAhead);
-      }
+      const uint64_t t = blk + i * G;
       const uint64_t base = t * kItems;
+      // the buffer of tile i + kAhead last held tile i - 1, whose reads all
+      // ended before the barrier of the previous step
+      if (tid == 0) start_load(i + kAhead);
       T run = 0;
       if (full_tile(t)) {
-        if (!mbar_wait(&s_bar[i % kStages], (uint32_t)((i / kStages) & 1u), timeout_ns))
+        if (!mbar_wait(&s_bar_load[i % kLoadBufs], (uint32_t)((i / kLoadBufs) & 1u), timeout_ns))
           set_status(&ctrl->status, PIP_ETIMEOUT);
-        const uint4* src = reinterpret_cast<const uint4*>(s_buf + (i % kStages) * kItems + tid * kPer);
+        const uint4* src = reinterpret_cast<const uint4*>(s_load + (i % kLoadBufs) * kItems + tid * kPer);
 #pragma unroll
         for (uint32_t q = 0; q < kPer / kVec; ++q) {
           const uint4 w = src[q];
           const T* e = reinterpret_cast<const T*>(&w);
 #pragma unroll
           for (uint32_t k = 0; k < kVec; ++k) {
-            vcur[q * kVec + k] = run;
+            vd[0][q * kVec + k] = run;
             run += e[k];
           }
         }
@@ -405,7 +476,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
 #pragma unroll
         for (uint32_t k = 0; k < kPer; ++k) {
           const uint64_t g = base + tid * kPer + k;
-          vcur[k] = run;
+          vd[0][k] = run;
           if (g < n) run += ldcg(A + g);
         }
       }
@@ -419,44 +490,48 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         agg += x;
         if (w < warp) woff += x;
       }
-      offcur = woff + (incl - run);
+      offd[0] = woff + (incl - run);
+      td[0] = t;
       if (tid == 0) {
         desc_publish<T>(ring + (t & (kRing - 1)), t, t == 0 ? kFlagPrefix : kFlagAgg, agg);
-        s_agg[i & 1u] = agg;
+        s_agg[i % kSlots] = agg;
+        mbar_arrive(&s_bar_agg[i % kSlots]);
       }
+      // s_warp is read by every scanning thread before it is written again
+      named_sync(kBarScan, kScanThreads);
+    } else {
+      named_sync(kBarScan, kScanThreads);  // the staging buffer is free (thread 0 waited)
     }
-    named_sync(kBarHandoff, kBlockThreads);  // H(i)
-    if (i >= 1) {
-      // finish tile i - 1 with the prefix the look-back warp found for it
-      const uint64_t ip = i - 1;
-      const T add = s_pre[ip & 1u] + offprev;
-      const uint64_t base = tprev * kItems;
-      if (full_tile(tprev)) {
-        T* tile = s_buf + (ip % kStages) * kItems;
-        uint4* dst = reinterpret_cast<uint4*>(tile + tid * kPer);
+    if (i >= kDefer) {
+      // finish tile j = i - kDefer with the prefix the look-back warp found
+      const uint64_t j = i - kDefer;
+      const uint32_t slot = (uint32_t)(j % kSlots);
+      if (!mbar_wait(&s_bar_pre[slot], (uint32_t)((j / kSlots) & 1u), timeout_ns))
+        set_status(&ctrl->status, PIP_ETIMEOUT);
+      const T add = s_pre[slot] + offd[kDefer];
+      const uint64_t tj = td[kDefer];
+      const uint64_t base = tj * kItems;
+      if (full_tile(tj)) {
+        uint4* dst = reinterpret_cast<uint4*>(s_stage + tid * kPer);
 #pragma unroll
         for (uint32_t q = 0; q < kPer / kVec; ++q) {
           uint4 w;
           T* e = reinterpret_cast<T*>(&w);
 #pragma unroll
-          for (uint32_t k = 0; k < kVec; ++k) e[k] = vprev[q * kVec + k] + add;
+          for (uint32_t k = 0; k < kVec; ++k) e[k] = vd[kDefer][q * kVec + k] + add;
           dst[q] = w;
         }
         fence_proxy_async();
         named_sync(kBarScan, kScanThreads);
-        if (tid == 0) bulk_store(A + base, tile, kTileBytes);
+        if (tid == 0) bulk_store(A + base, s_stage, kTileBytes);
       } else {
 #pragma unroll
         for (uint32_t k = 0; k < kPer; ++k) {
           const uint64_t g = base + tid * kPer + k;
-          if (g < n) stcg(A + g, (T)(vprev[k] + add));
+          if (g < n) stcg(A + g, (T)(vd[kDefer][k] + add));
         }
       }
     }
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) vprev[k] = vcur[k];
-    offprev = offcur;
-    tprev = t;
   }
   if (tid == 0) {
     bulk_wait_all();
@@ -478,6 +553,7 @@ int scan_blocks_per_sm() {
   auto it = cache.find(dev);
   if (it == cache.end()) {
     int per_sm = 0;
+    constexpr uint32_t kSmemBytes = ScanShape<T>::kSmemBytes;
     if (cudaFuncSetAttribute(scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel<T>, (int)kBlockThreads, kSmemBytes) !=
@@ -498,12 +574,14 @@ pip_status launch_scan(T* A, uint64_t n, T* total, void* aux, uint64_t timeout_n
   if (per_sm < 1) return PIP_ECUDA;
   uint32_t* latch = error_latch_ptr();
   if (latch == nullptr) return PIP_ECUDA;
-  // at most kRing / 8 blocks, so that the ring outlasts every look-back;
+  // at most kRing / (2 kDefer + 4) blocks, so that the ring outlasts every
+  // look-back (the indices in use span fewer than (2 kDefer + 3) G);
   // the tags hold 24 bits of the tile index, far more than the tiles in
   // flight
-  const uint64_t ntiles = (n + kTileBytes / sizeof(T) - 1) / (kTileBytes / sizeof(T));
+  constexpr uint64_t kItems = ScanShape<T>::kTileBytes / sizeof(T);
+  const uint64_t ntiles = (n + kItems - 1) / kItems;
   const uint32_t blocks = (uint32_t)std::max<uint64_t>(
-      1, std::min<uint64_t>({(uint64_t)per_sm * di.sms, (uint64_t)kRing / 8, ntiles}));
+      1, std::min<uint64_t>({(uint64_t)per_sm * di.sms, (uint64_t)kRing / (2u * kDefer + 4u), ntiles}));
   if (cudaMemsetAsync(aux, 0, scan_aux_bytes(), s) != cudaSuccess) return PIP_ECUDA;
   ScanCtrl* ctrl = static_cast<ScanCtrl*>(aux);
   ScanDesc* ring = reinterpret_cast<ScanDesc*>(static_cast<char*>(aux) + sizeof(ScanCtrl));
@@ -512,7 +590,7 @@ pip_status launch_scan(T* A, uint64_t n, T* total, void* aux, uint64_t timeout_n
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kBlockThreads);
-  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.dynamicSmemBytes = ScanShape<T>::kSmemBytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

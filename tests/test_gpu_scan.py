@@ -31,7 +31,7 @@ def expected(a: np.ndarray):
     return b, t
 
 
-TILE = {np.uint32: 14336, np.uint64: 7168}  # elements per 56 KB tile
+TILE = {np.uint32: 12288, np.uint64: 5120}  # elements per tile (48 KB for u32, 40 KB for u64)
 
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
