@@ -168,3 +168,19 @@ def test_list_and_tree_plans_obey_the_aux_bound(pip, eps, n):
         assert plan["aux_bytes"] + plan["smem_bytes"] <= plan["aux_bound_bytes"]
         assert plan["aux_bound_bytes"] == int(128 * n ** (1 - eps)) + 4096
     assert pip.tree_plan(n, eps)["elem_bytes"] == 32 and pip.tree_plan(n, eps)["driver"] == pip.DRIVER_TREE
+
+
+def test_host_stream_binding_checks_its_arguments(pip):
+    import torch
+
+    a = torch.zeros(16, dtype=torch.int64)
+    b = torch.zeros(8, dtype=torch.int64)
+    pip.shuffle_host_stream([], [], [])  # nothing to do
+    with pytest.raises(ValueError):
+        pip.shuffle_host_stream([a], [a, a], [1])  # lengths differ
+    with pytest.raises(ValueError):
+        pip.shuffle_host_stream([a, b], [a, b], [1, 2])  # shapes differ
+    with pytest.raises(ValueError):
+        pip.shuffle_host_stream([a], [a.to(torch.int32)], [1])  # dtypes differ
+    with pytest.raises(ValueError):
+        pip.shuffle_host_stream([a[::2]], [a[::2]], [1])  # not contiguous
