@@ -173,6 +173,7 @@ struct ListPlan {
   uint64_t smem_bytes = 0;  // all blocks' on-chip lists and caches (counted in the bound)
   uint64_t aux_bound = 0;
   uint32_t cache_per_thread = 0;  // bytes of on-chip cache per thread (tree contraction)
+  uint32_t cache_slot_bytes = 0;  // bytes per cached slot (tree contraction: 8 or 12)
   uint64_t block_smem() const { return 8ull * kloc + (uint64_t)cache_per_thread * threads; }
 };
 // The shape of a round-engine plan depends on its kernel's occupancy:

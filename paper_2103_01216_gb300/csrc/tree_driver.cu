@@ -64,11 +64,17 @@ constexpr uint32_t kTreeThreads = 512;
 #define PIP_TREE_PHASE_A_WIDTH 1
 #endif
 constexpr uint32_t kPhaseAWidth = PIP_TREE_PHASE_A_WIDTH;
-// A marked leaf's sibling and grandparent, found in phase A, are kept on chip
-// for phase B (slots q < qc of each thread, two 32-bit words each; which
-// child word of the grandparent to rewrite is a register bit), so that phase
-// B only writes.  Later slots read their records again.  qc is the largest of
-// 8, 4, 2, 1 that fits the scratch bound without lowering F.
+// A marked leaf's sibling, grandparent and (when room allows) parent, found
+// in phase A, are kept on chip for phase B (slots q < qc of each thread, two
+// or three 32-bit words each; which child word of the grandparent to rewrite
+// is a register bit), so that phase B only writes -- with the parent, the
+// leaf's whole 32-byte record at once, a full sector that L2 need not fetch
+// before writing it back.  Later slots read their records again.  The planner
+// takes the first of 8, 4, 2, 1 slots of three words, then of two, that fits
+// the scratch bound without lowering F.
+#ifndef PIP_TREE_CACHE_PARENT
+#define PIP_TREE_CACHE_PARENT 1
+#endif
 constexpr uint32_t kCacheSlotChoices[] = {8u, 4u, 2u, 1u};
 constexpr uint32_t kNil32 = 0xFFFFFFFFu;
 #ifndef PIP_TREE_MIN_BLOCKS
@@ -89,7 +95,8 @@ struct TreeArgs {
   uint64_t timeout_ns;
   uint64_t deadline_ns;
   uint32_t max_rounds;
-  uint32_t qc;  // cached slots per thread (0, 1, 2, 4 or 8)
+  uint32_t qc;         // cached slots per thread (0, 1, 2, 4 or 8)
+  uint32_t cache_par;  // 1: the cache holds the parent too (whole-record writes)
 };
 
 __device__ __forceinline__ uint64_t parent_of(const ulonglong2* h, uint64_t v) { return ldcg(&h[2 * v].x); }
@@ -109,14 +116,14 @@ __device__ __forceinline__ void tree_slice(uint32_t f, uint32_t* off, uint32_t* 
 // 2 when it is carried; *bad is set on a pointer that fails its check (that
 // node then counts as no work).  For a leaf that rakes, s_out[k] and g_out[k]
 // are its sibling and grandparent and g_right[k] tells that the parent is the
-// grandparent's right child.  The K nodes go through the dependent loads
+// grandparent's right child (p_out[k] its parent).  The K nodes go through the dependent loads
 // (own record, parent, sibling and grandparent, then the nephews' and
 // uncle's left words) stage by stage, so that a thread keeps K chains of
 // random reads in flight instead of one.
 template <int K>
 __device__ __forceinline__ void tree_decide(const ulonglong2* h, const uint64_t (&i)[K], const bool (&act)[K],
-                                            uint64_t n, bool* bad, uint32_t (&d)[K], uint64_t (&s_out)[K],
-                                            uint64_t (&g_out)[K], bool (&g_right)[K]) {
+                                            uint64_t n, bool* bad, uint32_t (&d)[K], uint64_t (&p_out)[K],
+                                            uint64_t (&s_out)[K], uint64_t (&g_out)[K], bool (&g_right)[K]) {
   bool live[K];
   uint64_t p[K];
 #pragma unroll
@@ -209,6 +216,7 @@ __device__ __forceinline__ void tree_decide(const ulonglong2* h, const uint64_t 
   for (int k = 0; k < K; ++k) {
     if (!live[k]) continue;
     d[k] = (win[k] && !l0[k] && !l1[k] && !lu[k]) ? 1u : 2u;
+    p_out[k] = p[k];
     s_out[k] = s[k];
     g_out[k] = g[k];
     g_right[k] = g[k] != kNil && gr[k] == p[k];
@@ -233,15 +241,17 @@ __device__ __forceinline__ bool tree_rake(ulonglong2* h, uint64_t i, uint32_t r,
     if (left_of(h, g) == p) stcg(&h[2 * g].y, (u64)s);
     else stcg(&h[2 * g + 1].x, (u64)s);
   }
-  stcg(&h[2 * i].y, (u64)s);
+  // the leaf's whole record (its parent word is unchanged): a full sector
+  stcg(&h[2 * i], make_ulonglong2((u64)p, (u64)s));
   stcg(&h[2 * i + 1], make_ulonglong2(g, (unsigned long long)r + 1ull));
   return true;
 }
 
 __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds_kernel(const TreeArgs a) {
   extern __shared__ uint32_t s_loc[];  // two on-chip lists of a.kloc carried leaves, then the cache
-  uint32_t* const c_sib = s_loc + 2u * a.kloc;      // [a.qc][blockDim.x]
-  uint32_t* const c_gp = c_sib + a.qc * blockDim.x;  // [a.qc][blockDim.x]
+  uint32_t* const c_sib = s_loc + 2u * a.kloc;       // [a.qc][blockDim.x]
+  uint32_t* const c_gp = c_sib + a.qc * blockDim.x;   // [a.qc][blockDim.x]
+  uint32_t* const c_par = c_gp + a.qc * blockDim.x;   // [a.qc][blockDim.x]
   __shared__ uint32_t s_nloc[2];
   __shared__ uint32_t s_lcount, s_err;
   __shared__ uint32_t s_U, s_f, s_g, s_m, s_stop;
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
       uint64_t iv[kPhaseAWidth];
       bool act[kPhaseAWidth];
       uint32_t d[kPhaseAWidth];
-      uint64_t sib[kPhaseAWidth], gp[kPhaseAWidth];
+      uint64_t par[kPhaseAWidth], sib[kPhaseAWidth], gp[kPhaseAWidth];
       bool g_right[kPhaseAWidth];
 #pragma unroll
       for (uint32_t k = 0; k < kPhaseAWidth; ++k) {
@@ -335,13 +345,14 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
         iv[k] = ii;
       }
       bool bad = false;
-      tree_decide<(int)kPhaseAWidth>(h, iv, act, a.n, &bad, d, sib, gp, g_right);
+      tree_decide<(int)kPhaseAWidth>(h, iv, act, a.n, &bad, d, par, sib, gp, g_right);
       if (bad) fail(PIP_EINVAL);
 #pragma unroll
       for (uint32_t k = 0; k < kPhaseAWidth; ++k) {
         const uint32_t q = q0 + k;
         if (q >= nq) break;  // uniform: nq is the same for the whole block
         if (d[k] == 1u && q < a.qc) {
+          if (a.cache_par) c_par[q * NT + threadIdx.x] = (uint32_t)par[k];
           c_sib[q * NT + threadIdx.x] = (uint32_t)sib[k];
           c_gp[q * NT + threadIdx.x] = gp[k] == kNil ? kNil32 : (uint32_t)gp[k];
           if (g_right[k]) rights |= 1u << q;
@@ -430,10 +441,11 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
       if (q < a.qc) {
         // cached: only writes (the values were checked in phase A)
         using u64 = unsigned long long;
+        const uint64_t par = a.cache_par ? (uint64_t)c_par[q * NT + threadIdx.x] : 0u;
         const uint64_t sib = c_sib[q * NT + threadIdx.x];
         const uint32_t g32 = c_gp[q * NT + threadIdx.x];
         const uint64_t gp = g32 == kNil32 ? kNil : (uint64_t)g32;
-        if (sib >= a.n || (gp != kNil && gp >= a.n)) {
+        if (par >= a.n || sib >= a.n || (gp != kNil && gp >= a.n)) {
           fail(PIP_EINTERNAL);
           continue;
         }
@@ -442,7 +454,10 @@ __global__ void __launch_bounds__(kTreeThreads, PIP_TREE_MIN_BLOCKS) tree_rounds
           if ((rights >> q) & 1u) stcg(&h[2 * gp + 1].x, (u64)sib);
           else stcg(&h[2 * gp].y, (u64)sib);
         }
-        stcg(&h[2 * (uint64_t)i].y, (u64)sib);
+        // the leaf's record: whole when the parent is cached (its parent word
+        // is unchanged), else from the left word on
+        if (a.cache_par) stcg(&h[2 * (uint64_t)i], make_ulonglong2((u64)par, (u64)sib));
+        else stcg(&h[2 * (uint64_t)i].y, (u64)sib);
         stcg(&h[2 * (uint64_t)i + 1], make_ulonglong2((u64)gp, (u64)r + 1ull));
       } else if (!tree_rake(h, i, r, a.n)) {
         fail(PIP_EINTERNAL);
@@ -552,11 +567,15 @@ pip_status make_tree_plan(uint64_t n, double eps, const pip_options* opt, ListPl
   pip_status st = make_list_plan(n, eps, &o, &plain, &tree_blocks_per_sm, 0);
   if (st != PIP_OK) return st;
   *out = plain;
-  for (const uint32_t qc : kCacheSlotChoices) {
-    ListPlan cached;
-    if (make_list_plan(n, eps, &o, &cached, &tree_blocks_per_sm, 8u * qc) == PIP_OK && cached.F == plain.F) {
-      *out = cached;
-      break;
+  for (const uint32_t words : {PIP_TREE_CACHE_PARENT ? 3u : 2u, 2u}) {
+    for (const uint32_t qc : kCacheSlotChoices) {
+      ListPlan cached;
+      if (make_list_plan(n, eps, &o, &cached, &tree_blocks_per_sm, 4u * words * qc) == PIP_OK &&
+          cached.F == plain.F) {
+        cached.cache_slot_bytes = 4u * words;
+        *out = cached;
+        return PIP_OK;
+      }
     }
   }
   return PIP_OK;
@@ -579,7 +598,8 @@ pip_status launch_tree_driver(const ListPlan& plan, void* rec, void* aux, pip_st
   a.timeout_ns = plan.timeout_ns;
   a.deadline_ns = plan.deadline_ns;
   a.max_rounds = plan.n + 8u;
-  a.qc = plan.cache_per_thread / 8u;
+  a.cache_par = plan.cache_slot_bytes == 12u ? 1u : 0u;
+  a.qc = plan.cache_slot_bytes != 0u ? plan.cache_per_thread / plan.cache_slot_bytes : 0u;
   if (cudaMemsetAsync(aux, 0, plan.aux_bytes, stream) != cudaSuccess) return PIP_ECUDA;
   if (plan.flags & PIP_FLAG_VALIDATE_INPUT) {
     const uint32_t vb = (uint32_t)std::min<uint64_t>(1024, (plan.n + 255) / 256);
