@@ -158,13 +158,10 @@ __device__ __forceinline__ void desc_publish(ScanDesc* d, uint64_t tile, uint64_
 // out -- still a correct value, the walk just goes further back.  The
 // single-lane poll of one descriptor (kStrong = true) uses relaxed loads,
 // which the compiler may not hoist out of the polling loop.
-#ifndef PIP_SCAN_DESC_V2
-#define PIP_SCAN_DESC_V2 1
-#endif
 template <typename T, bool kStrong = false>
 __device__ __forceinline__ uint64_t desc_read(const ScanDesc* d, uint64_t tile, T* value) {
   unsigned long long a, b;
-  if (PIP_SCAN_DESC_V2 && !kStrong) {
+  if (!kStrong) {
     const ulonglong2 ab = __ldcg(reinterpret_cast<const ulonglong2*>(d));
     a = ab.x;
     b = ab.y;
