@@ -67,7 +67,7 @@ typedef struct {
     double eps;
     uint32_t fresh_per_round;  /* F: fresh swaps added to the prefix each round, ~C*n^(1-eps) */
     uint32_t max_active;       /* k: cap on the swaps active in one round (F plus carried losers) */
-    uint32_t slots;            /* reservation slots per round table */
+    uint32_t slots;            /* reservation slots per round table (tree plans: phase-B cache bytes per thread) */
     uint32_t grid_blocks;      /* persistent blocks launched (0 = decided at launch) */
     uint32_t block_threads;
     uint64_t aux_bytes;        /* exact device scratch bytes this plan allocates */
@@ -540,7 +540,10 @@ pip_status pip_tree_contract_ex(pip_tree_node *nodes_dev, uint64_t n, double eps
 /* pip_tree_plan -- the plan pip_tree_contract_ex would use (host only):
  * elem_bytes = 32, fresh_per_round (F), max_active (kmax), grid_blocks,
  * block_threads, aux_bytes, smem_bytes, aux_bound_bytes, min_rounds;
- * driver = 4. */
+ * driver = 4.  `slots` holds the on-chip phase-B cache per thread in bytes
+ * (counted in smem_bytes): 12 per cached leaf when the leaf's parent, sibling
+ * and grandparent are kept, 8 when only the last two are, 0 for no cache.
+ * The results never depend on it. */
 pip_status pip_tree_plan(uint64_t n, double eps, const pip_options *opt, pip_plan_info *out);
 
 /* ------------------------------------------------------------ scan */

@@ -655,6 +655,7 @@ pip_status pip_tree_plan(uint64_t n, double eps, const pip_options* opt, pip_pla
   out->smem_bytes = p.smem_bytes;
   out->aux_bound_bytes = p.aux_bound;
   out->min_rounds = (n + p.F - 1) / p.F;
+  out->slots = p.cache_per_thread;
   return PIP_OK;
 }
 

@@ -167,7 +167,33 @@ def test_list_and_tree_plans_obey_the_aux_bound(pip, eps, n):
         assert plan["max_active"] == F * 5 // 2 + 2
         assert plan["aux_bytes"] + plan["smem_bytes"] <= plan["aux_bound_bytes"]
         assert plan["aux_bound_bytes"] == int(128 * n ** (1 - eps)) + 4096
-    assert pip.tree_plan(n, eps)["elem_bytes"] == 32 and pip.tree_plan(n, eps)["driver"] == pip.DRIVER_TREE
+    tp = pip.tree_plan(n, eps)
+    assert tp["elem_bytes"] == 32 and tp["driver"] == pip.DRIVER_TREE
+    # the phase-B cache: 8 slots at most, 12 or 8 bytes each, counted on chip
+    assert tp["slots"] in (0, 8, 16, 32, 64, 12, 24, 48, 96)
+    assert tp["smem_bytes"] >= tp["grid_blocks"] * tp["block_threads"] * tp["slots"]
+
+
+def test_tree_plan_takes_the_largest_cache_that_fits(pip):
+    # The phase-B cache per thread is the first of 8, 4, 2, 1 three-word
+    # slots, then 8, 4, 2, 1 two-word slots, that fits the scratch bound
+    # beside the plan (F fixed here); so the next larger choice must not fit.
+    # The on-chip lists do not depend on the cache, so the plan's own figures
+    # give what every other choice would cost.
+    n, eps, F = 262142, 0.25, 40000
+    seen = []
+    for gb in (16, 24, 38, 48, 64, 76, 100, 152):
+        plan = pip.tree_plan(n, eps, grid_blocks=gb, fresh_per_round=F)
+        assert plan["fresh_per_round"] == F and plan["grid_blocks"] == gb
+        c, threads = plan["slots"], gb * plan["block_threads"]
+        seen.append(c)
+        base = plan["aux_bytes"] + plan["smem_bytes"] - threads * c  # the plan without a cache
+        assert base + threads * c <= plan["aux_bound_bytes"]
+        order = [96, 48, 24, 12, 64, 32, 16, 8, 0]
+        for larger in order[:order.index(c)]:
+            assert base + threads * larger > plan["aux_bound_bytes"], (gb, c, larger)
+    assert seen == sorted(seen, key=lambda c: [96, 48, 24, 12, 64, 32, 16, 8, 0].index(c)), seen
+    assert any(c % 12 == 0 and c for c in seen) and 8 in seen and 0 in seen, seen
 
 
 def test_host_stream_binding_checks_its_arguments(pip):

@@ -228,15 +228,47 @@ def test_large_forest_in_the_bench_launch(pip):
 
 @pytest.mark.parametrize("opts", [dict(grid_blocks=152, fresh_per_round=400000), dict(grid_blocks=38)])
 def test_phase_b_cache_path(pip, opts):
-    # Plans whose blocks keep the on-chip phase-B cache (64 bytes per thread,
-    # counted in smem_bytes): with 152 blocks every marked leaf's phase B is
-    # writes only; with 38 blocks threads hold more than the eight cached
-    # slots, so the cached and the re-reading paths run in the same rounds.
+    # Plans whose blocks keep the on-chip phase-B cache (eight slots of 12 or
+    # 8 bytes per thread, counted in smem_bytes): with 152 blocks every marked
+    # leaf's phase B is writes only; with 38 blocks threads hold more than the
+    # eight cached slots, so the cached and the re-reading paths run in the
+    # same rounds.
     rec = workloads.random_tree((1 << 20) + 7, rng_seed=77, trees=3)
     n = rec.shape[0]
     F, plan = plan_F(pip, n, 0.1, **opts)
     assert plan["smem_bytes"] >= plan["grid_blocks"] * plan["block_threads"] * 64, plan
     out, st = gpu_contract(pip, rec, eps=0.1, with_stats=True, **opts)
+    assert st.status == 0
+    assert np.array_equal(out, expected(rec, F))
+    rc, back = oracle.tree_uncontract(out, rec)
+    assert rc == 0 and np.array_equal(back, rec)
+
+
+@pytest.mark.parametrize("cache", [12, 8, 0])
+def test_each_phase_b_cache_format(pip, cache):
+    # The planner caches a marked leaf's parent, sibling and grandparent (12
+    # bytes a slot) where they fit the scratch bound, else only the last two
+    # (8 bytes: phase B then rewrites the record from its left word on), else
+    # nothing; the plan reports which in `slots`.  A plan of each format is
+    # looked up by grid size and eps, and must give the oracle's records.
+    rec = workloads.random_tree(1 << 17, rng_seed=5, trees=2)
+    n = rec.shape[0]
+    for eps in (0.1, 0.25, 0.5):
+        for gb in (4, 8, 16, 38, 76, 152):
+            plan = pip.tree_plan(n, eps, grid_blocks=gb)
+            c = plan["slots"]
+            fmt = 12 if c and c % 12 == 0 else (8 if c else 0)
+            if fmt == cache:
+                break
+        else:
+            continue
+        break
+    else:
+        pytest.fail(f"no plan with a {cache}-byte cache slot")
+    assert plan["smem_bytes"] >= plan["grid_blocks"] * plan["block_threads"] * c
+    F = plan["fresh_per_round"]
+    assert plan["max_active"] == kmax_of(F)
+    out, st = gpu_contract(pip, rec, eps=eps, with_stats=True, grid_blocks=gb)
     assert st.status == 0
     assert np.array_equal(out, expected(rec, F))
     rc, back = oracle.tree_uncontract(out, rec)
