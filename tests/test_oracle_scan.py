@@ -66,19 +66,25 @@ MUTATIONS = {
     "down_right_gets_p": ("    down64(a, k + 1, t, p + left);", "    down64(a, k + 1, t, p);"),
     "inclusive_leaf": ("    if (s == t) {\n        a[s] = p;\n        return;\n    }\n    const uint64_t k = (s + t) / 2;\n    const uint64_t left",
                        "    if (s == t) {\n        a[s] = p + a[s];\n        return;\n    }\n    const uint64_t k = (s + t) / 2;\n    const uint64_t left"),
+    # the 32-bit path and the total
+    "u32_up_adds_wrong_cell": ("    a[t] += a[k];\n}\n\nstatic void down32", "    a[t] += a[k + 1];\n}\n\nstatic void down32"),
+    "u32_down_right_gets_p": ("    down32(a, k + 1, t, p + left);", "    down32(a, k + 1, t, p);"),
+    "u32_left_gets_left_sum": ("    down32(a, s, k, p);", "    down32(a, s, k, p + left);"),
+    "total_read_after_down": ("    *total = a[n - 1];\n    down64(a, 0, n - 1, 0);", "    down64(a, 0, n - 1, 0);\n    *total = a[n - 1];"),
 }
 
 
 def _scan_pins_pass(path):
     L = ctypes.CDLL(path)
-    L.oracle_scan_u64.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
-    for n in (1, 2, 3, 5, 8, 13, 100):
-        a = np.arange(1, n + 1, dtype=np.uint64) * np.uint64(3)
-        want = exclusive_by_definition(a)
-        tot = np.zeros(1, dtype=np.uint64)
-        L.oracle_scan_u64(a.ctypes.data, n, tot.ctypes.data)
-        if not np.array_equal(a, want) or int(tot[0]) != 3 * n * (n + 1) // 2:
-            return False
+    for fn, dtype in ((L.oracle_scan_u64, np.uint64), (L.oracle_scan_u32, np.uint32)):
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+        for n in (1, 2, 3, 5, 8, 13, 100):
+            a = np.arange(1, n + 1, dtype=dtype) * dtype(3)
+            want = exclusive_by_definition(a)
+            tot = np.zeros(1, dtype=dtype)
+            fn(a.ctypes.data, n, tot.ctypes.data)
+            if not np.array_equal(a, want) or int(tot[0]) != 3 * n * (n + 1) // 2:
+                return False
     return True
 
 
