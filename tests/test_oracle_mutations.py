@@ -147,6 +147,7 @@ LIST_MUTATIONS = {
         "for (uint64_t i = n; i-- > 0;) {\n        const uint64_t p = rec[2 * i], q = rec[2 * i + 1];\n"
         "        if (p != ORACLE_NIL) {\n            if (p >= n) return -1;"),
     "successor_gets_successor": ("rec[2 * q] = p;", "rec[2 * q] = q;"),
+    "predecessor_gets_predecessor": ("rec[2 * p + 1] = q;", "rec[2 * p + 1] = p;"),
 }
 
 
