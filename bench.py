@@ -179,6 +179,50 @@ def cpu_oracle_sample(dtype: str, seed: int, n_sample: int):
     return n_sample / dt, dt
 
 
+def cpu_oracle_workload(kind: str, eps: float, seed: int, n_sample: int, dtype: str = "u64"):
+    """The oracle of a list, tree or scan workload, timed as it stands on one
+    host thread over a bounded sample of the same shape (one random list, one
+    random binary tree of n_sample leaves, or n_sample integers below 2^20);
+    input generation is outside the timed region.  Returns the
+    ``cpu_baseline`` object."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    oracle.build()
+    if kind == "list":
+        rec = workloads.random_lists(n_sample, rng_seed=seed)
+        t0 = time.perf_counter()
+        oracle.list_contract(rec)
+        dt = time.perf_counter() - t0
+        units, unit = n_sample, "nodes/s"
+        what = f"sequential splice in index order (oracle/listc.c) of one random list of {n_sample} nodes"
+    elif kind == "tree":
+        import paper_2103_01216_gb300 as pip
+
+        rec = workloads.random_tree(n_sample, rng_seed=seed)
+        F = pip.tree_plan(rec.shape[0], eps)["fresh_per_round"]
+        t0 = time.perf_counter()
+        oracle.tree_contract(rec, F, F * 5 // 2 + 2)
+        dt = time.perf_counter() - t0
+        units, unit = rec.shape[0], "nodes/s"
+        what = (f"round schedule (oracle/treec.c) of one random binary tree of {rec.shape[0]} nodes, "
+                f"F = {F}, eps {eps}")
+    elif kind == "scan":
+        npdt = np.uint32 if dtype == "u32" else np.uint64
+        a = np.random.default_rng(seed).integers(0, 1 << 20, size=n_sample, dtype=npdt)
+        t0 = time.perf_counter()
+        oracle.scan_exclusive(a)
+        dt = time.perf_counter() - t0
+        units, unit = n_sample, "elems/s"
+        what = f"up-sweep / down-sweep recursion (oracle/scanc.c) of {n_sample} {dtype} values"
+    else:
+        raise ValueError(kind)
+    return {"value": units / dt, "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": f"{what}, one host thread, {dt:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -486,6 +530,8 @@ def run_list(args):
         "paper_context": {"pip_72cores_ht_200M_ms": PAPER_LIST_PIP_200M_MS},
         "gpu_launches": args.steps, "clocks": clk.summary(), "step_ms": times,
     }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_workload("list", eps, args.seed, min(n, 1 << 25))
     print(json.dumps(line), flush=True)
     return 0
 
@@ -613,6 +659,8 @@ def run_tree(args):
         "paper_context": {"pip_72cores_ht_200M_ms": PAPER_TREE_PIP_200M_MS},
         "gpu_launches": args.steps, "clocks": clk.summary(), "step_ms": times,
     }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_workload("tree", eps, args.seed, min(leaves, 1 << 23))
     print(json.dumps(line), flush=True)
     return 0
 
@@ -664,6 +712,8 @@ def run_scan(args):
                      "algorithmic_bytes_per_elem": SCAN_BYTES_PER_ELEM[dt]},
         "aux_bytes": pip.scan_aux_bytes(), "gpu_launches": args.steps, "clocks": clk.summary(), "step_ms": times,
     }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_workload("scan", 0.0, args.seed, min(n, 1 << 28), dt)
     print(json.dumps(line), flush=True)
     return 0
 
