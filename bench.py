@@ -179,12 +179,15 @@ def cpu_oracle_sample(dtype: str, seed: int, n_sample: int):
     return n_sample / dt, dt
 
 
-def cpu_oracle_workload(kind: str, eps: float, seed: int, n_sample: int, dtype: str = "u64"):
+def cpu_oracle_workload(kind: str, eps: float, seed: int, n_sample: int, dtype: str = "u64",
+                        min_seconds: float = 5.0, max_reps: int = 10):
     """The oracle of a list, tree or scan workload, timed as it stands on one
     host thread over a bounded sample of the same shape (one random list, one
-    random binary tree of n_sample leaves, or n_sample integers below 2^20);
-    input generation is outside the timed region.  Returns the
-    ``cpu_baseline`` object."""
+    random binary tree of n_sample leaves, or n_sample integers below 2^20).
+    The oracle works in place, so it runs on a fresh copy of the one input
+    each time (copies and input generation outside the timed region), until
+    min_seconds of timed work or max_reps runs.  Returns the ``cpu_baseline``
+    object."""
     import numpy as np
 
     import oracle
@@ -192,35 +195,36 @@ def cpu_oracle_workload(kind: str, eps: float, seed: int, n_sample: int, dtype: 
 
     oracle.build()
     if kind == "list":
-        rec = workloads.random_lists(n_sample, rng_seed=seed)
-        t0 = time.perf_counter()
-        oracle.list_contract(rec)
-        dt = time.perf_counter() - t0
+        src = workloads.random_lists(n_sample, rng_seed=seed)
+        run = oracle.list_contract
         units, unit = n_sample, "nodes/s"
         what = f"sequential splice in index order (oracle/listc.c) of one random list of {n_sample} nodes"
     elif kind == "tree":
         import paper_2103_01216_gb300 as pip
 
-        rec = workloads.random_tree(n_sample, rng_seed=seed)
-        F = pip.tree_plan(rec.shape[0], eps)["fresh_per_round"]
-        t0 = time.perf_counter()
-        oracle.tree_contract(rec, F, F * 5 // 2 + 2)
-        dt = time.perf_counter() - t0
-        units, unit = rec.shape[0], "nodes/s"
-        what = (f"round schedule (oracle/treec.c) of one random binary tree of {rec.shape[0]} nodes, "
+        src = workloads.random_tree(n_sample, rng_seed=seed)
+        F = pip.tree_plan(src.shape[0], eps)["fresh_per_round"]
+        run = lambda rec: oracle.tree_contract(rec, F, F * 5 // 2 + 2)  # noqa: E731
+        units, unit = src.shape[0], "nodes/s"
+        what = (f"round schedule (oracle/treec.c) of one random binary tree of {src.shape[0]} nodes, "
                 f"F = {F}, eps {eps}")
     elif kind == "scan":
         npdt = np.uint32 if dtype == "u32" else np.uint64
-        a = np.random.default_rng(seed).integers(0, 1 << 20, size=n_sample, dtype=npdt)
-        t0 = time.perf_counter()
-        oracle.scan_exclusive(a)
-        dt = time.perf_counter() - t0
+        src = np.random.default_rng(seed).integers(0, 1 << 20, size=n_sample, dtype=npdt)
+        run = oracle.scan_exclusive
         units, unit = n_sample, "elems/s"
         what = f"up-sweep / down-sweep recursion (oracle/scanc.c) of {n_sample} {dtype} values"
     else:
         raise ValueError(kind)
-    return {"value": units / dt, "unit": unit, "cores": 1, "kind": "oracle",
-            "sample": f"{what}, one host thread, {dt:.1f} s"}
+    total, reps = 0.0, 0
+    while reps < max_reps and (reps == 0 or total < min_seconds):
+        work = src.copy()
+        t0 = time.perf_counter()
+        run(work)
+        total += time.perf_counter() - t0
+        reps += 1
+    return {"value": units * reps / total, "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": f"{what}, {reps} runs on copies of one input, one host thread, {total:.1f} s"}
 
 
 def run_reference(args):
