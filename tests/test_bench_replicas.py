@@ -50,3 +50,17 @@ def test_single_process_is_identity():
 
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.replica_throughput(10, 1, 1, 1000.0) == 10.0
+
+
+@pytest.mark.parametrize("kind,dtype", [("list", "u64"), ("tree", "u64"), ("scan", "u32"), ("scan", "u64")])
+def test_workload_cpu_baseline_is_a_bounded_oracle_timing(kind, dtype):
+    # The list, tree and scan lines time their oracle on one host thread over
+    # a bounded sample, repeating on copies of one input up to a cap.
+    import bench
+
+    cb = bench.cpu_oracle_workload(kind, 0.5, 3, 4096, dtype, min_seconds=0.05, max_reps=3)
+    assert set(cb) == {"value", "unit", "cores", "kind", "sample"}
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    assert cb["unit"] == ("elems/s" if kind == "scan" else "nodes/s")
+    reps = int(cb["sample"].split(" runs on copies")[0].rsplit(", ", 1)[1])
+    assert 1 <= reps <= 3
