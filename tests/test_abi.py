@@ -210,3 +210,25 @@ def test_host_stream_binding_checks_its_arguments(pip):
         pip.shuffle_host_stream([a], [a.to(torch.int32)], [1])  # dtypes differ
     with pytest.raises(ValueError):
         pip.shuffle_host_stream([a[::2]], [a[::2]], [1])  # not contiguous
+
+
+def test_device_entry_points_refuse_host_tensors(pip):
+    # No CPU fallback: every device entry point rejects a host tensor before
+    # any launch, and leaves it untouched.
+    import torch
+
+    a = torch.arange(64, dtype=torch.int64)
+    lists = torch.full((8, 2), -1, dtype=torch.int64)
+    trees = torch.full((7, 4), -1, dtype=torch.int64)
+    calls = [
+        lambda: pip.shuffle(a, seed=1),
+        lambda: pip.shuffle_batch([a, a], [1, 2]),
+        lambda: pip.list_contract(lists),
+        lambda: pip.tree_contract(trees),
+        lambda: pip.scan(a),
+    ]
+    for call in calls:
+        with pytest.raises((ValueError, pip.PipError)):
+            call()
+    assert torch.equal(a, torch.arange(64, dtype=torch.int64))
+    assert bool((lists == -1).all()) and bool((trees == -1).all())
