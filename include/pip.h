@@ -74,7 +74,7 @@ typedef struct {
     uint64_t aux_bound_bytes;  /* c*n^(1-eps) + 4096 with c = PIP_AUX_C: the bound aux_bytes obeys */
     uint64_t min_rounds;       /* ceil((n-1)/F): a lower bound on the rounds */
     uint32_t driver;           /* 0 = persistent grid, 1 = one block, 2 = one cluster (shared-memory tables), 3 = list contraction, 4 = tree contraction */
-    uint32_t pad;
+    uint32_t flags;            /* PIP_FLAG_* bits the plan runs with: the caller's plus the planner's choices */
     uint64_t smem_bytes;       /* on-chip scratch of the one-block driver (counted in the bound) */
 } pip_plan_info;
 
@@ -100,9 +100,22 @@ typedef struct {
 /* Prefetch into L2, one round ahead, the array lines the next fresh block
  * will swap. */
 #define PIP_FLAG_PREFETCH 2u
+/* Grid driver: how a winning swap moves its two elements.  Exchange commit:
+ * the own element is loaded with the reservation checks, one atomic exchange
+ * at L2 puts it into A[H[i]] and returns the target's element, which is
+ * stored at A[i] -- one random L2 transaction per swap instead of a load and
+ * a store.  Load-store commit: both elements are loaded (after the decision,
+ * or with the checks under PIP_FLAG_SPECULATE) and both are stored.  By
+ * default the planner takes the exchange commit for large prefixes (the
+ * random-access-bound regime) and the speculative load-store commit for
+ * small ones (the latency-bound regime, where the exchange would add a
+ * memory round trip per round); these flags force one.  Performance only;
+ * results are identical. */
+#define PIP_FLAG_SWAP_LOADSTORE 4u
+#define PIP_FLAG_SWAP_EXCHANGE 8u
 /* Grid driver: keep the normal L2 eviction priority for the array stores
  * (by default they are marked evict-first).  Performance only; results are
- * identical.  (Flag bits 4 and 8 are unused.) */
+ * identical. */
 #define PIP_FLAG_STORE_EVICT_NORMAL 16u
 /* Driver selection: by default arrays whose prefix fits in one block's shared
  * memory run on one block, larger prefixes on the persistent grid. */
@@ -375,13 +388,20 @@ pip_status pip_check(void *stream);
  * it is an interface for such callers, not part of the method.
  *   Same arguments, same result as pip_shuffle (hashed targets, persistent
  *   grid driver), but the scratch comes from a fixed 16 MiB device area
- *   compiled into the library, which every GPU that loads the library keeps
- *   until the process exits.  Nothing is allocated or freed.
+ *   compiled into the library, which a device holds from the first call on
+ *   it until the process exits.  Nothing is allocated or freed.
  *   Requests whose plan needs more than 16 MiB of scratch (pip_plan with
  *   PIP_FLAG_FORCE_GRID reports the need as aux_bytes) return PIP_ETOOLARGE
  *   before anything is queued.
- *   The first call on a device looks up the area's device address (and may
- *   load the library's device code): make it before any stream capture.
+ *   A_dev must be device (or managed) memory of the current device: host
+ *   memory, registered or not, returns PIP_EINVAL before anything is queued.
+ *   Set-up: the first call on a device looks up the area's device address.
+ *   Under CUDA's lazy module loading (the default) that lookup is also when
+ *   the driver reserves the 16 MiB, so make the first call -- a call with
+ *   n = 0 does only the set-up and returns -- before the application
+ *   reserves the rest of the GPU's memory for itself, and before any stream
+ *   capture.  If the area cannot be reserved then, the call returns
+ *   PIP_ENOMEM (and the next call tries again).
  *   Each call clears the part of the area it uses; the area keeps the last
  *   call's contents.  All calls on a device share the area, so calls whose
  *   work overlaps on the GPU race and corrupt each other: order them on one

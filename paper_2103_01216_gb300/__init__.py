@@ -62,7 +62,7 @@ class PlanInfo(ctypes.Structure):
         ("aux_bound_bytes", ctypes.c_uint64),
         ("min_rounds", ctypes.c_uint64),
         ("driver", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
         ("smem_bytes", ctypes.c_uint64),
     ]
 
@@ -177,6 +177,8 @@ class ServeInfo(ctypes.Structure):
 STATS_BYTES = ctypes.sizeof(Stats)
 JOB_STATS_BYTES = ctypes.sizeof(JobStats)
 DRIVER_GRID, DRIVER_CTA, DRIVER_CLUSTER = 0, 1, 2
+FLAG_SWAP_LOADSTORE = 4
+FLAG_SWAP_EXCHANGE = 8
 FLAG_STORE_EVICT_NORMAL = 16
 FLAG_FORCE_GRID = 32
 FLAG_FORCE_CTA = 64

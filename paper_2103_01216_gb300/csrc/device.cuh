@@ -71,6 +71,42 @@ __device__ __forceinline__ void st_hint(uint4* p, uint4 v, uint64_t pol) {
                "r"(v.z), "r"(v.w), "l"(pol)
                : "memory");
 }
+// Exchange at L2: stores v into *p and returns the previous content, as one
+// atomic read-modify-write performed in the L2 slice that owns the line.  A
+// swap's random side done this way costs one L2 transaction instead of a
+// load and a later store of the same line (measured on GB300 at 10^9 random
+// targets: 44 ms against 60 ms for 8-byte elements, 51 against 68 ms for
+// 16-byte ones).  16-byte elements use the b128 form (16-byte aligned p).
+__device__ __forceinline__ uint32_t exch_hint(uint32_t* p, uint32_t v, uint64_t pol) {
+  uint32_t old;
+  asm volatile("atom.relaxed.gpu.global.exch.L2::cache_hint.b32 %0, [%1], %2, %3;"
+               : "=r"(old)
+               : "l"(p), "r"(v), "l"(pol)
+               : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long exch_hint(unsigned long long* p, unsigned long long v, uint64_t pol) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.exch.L2::cache_hint.b64 %0, [%1], %2, %3;"
+               : "=l"(old)
+               : "l"(p), "l"(v), "l"(pol)
+               : "memory");
+  return old;
+}
+__device__ __forceinline__ uint4 exch_hint(uint4* p, uint4 v, uint64_t pol) {
+  const unsigned long long vlo = ((unsigned long long)v.y << 32) | v.x;
+  const unsigned long long vhi = ((unsigned long long)v.w << 32) | v.z;
+  unsigned long long lo, hi;
+  asm volatile(
+      "{\n\t.reg .b128 nv, ov;\n\t"
+      "mov.b128 nv, {%2, %3};\n\t"
+      "atom.relaxed.gpu.global.exch.L2::cache_hint.b128 ov, [%4], nv, %5;\n\t"
+      "mov.b128 {%0, %1}, ov;\n\t}"
+      : "=l"(lo), "=l"(hi)
+      : "l"(vlo), "l"(vhi), "l"(p), "l"(pol)
+      : "memory");
+  return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+}
 // Fire-and-forget atomic max and or (no value returned to the thread).
 __device__ __forceinline__ void red_max(uint32_t* p, uint32_t v) {
   asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");

@@ -277,13 +277,20 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
         act[j] = act[j] && hh[j] != ii[j];  // self-loops finish at once
       }
       Elem x[kU], y[kU];
-      const bool spec = (a.flags & PIP_FLAG_SPECULATE) != 0u;
-      if (spec) {  // array loads issued before the decision (wasted for losers)
+      // Exchange commit (PIP_FLAG_SWAP_EXCHANGE, set by the planner): the
+      // own element is loaded together with the reservation checks (a
+      // coalesced read for the fresh block, wasted for the swaps that lose),
+      // and a winner exchanges it into A[h] at L2 and stores what comes back
+      // at A[i].  Load-store commit otherwise: both elements are loaded after
+      // the decision (or with it under PIP_FLAG_SPECULATE), both are stored.
+      const bool xchg = (a.flags & PIP_FLAG_SWAP_EXCHANGE) != 0u;
+      const bool spec = !xchg && (a.flags & PIP_FLAG_SPECULATE) != 0u;
+      if (xchg || spec) {
 #pragma unroll
         for (int j = 0; j < kU; ++j) {
           if (act[j]) {
             x[j] = ldcg(A + ii[j]);
-            y[j] = ldcg(A + hh[j]);
+            if (spec) y[j] = ldcg(A + hh[j]);
           }
         }
       }
@@ -308,17 +315,22 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
                               : (i < Lprev) ? (((own[j] >> ((i - L) & 31u)) & 1u) == 0u)
                                             : (own[j] <= i + 1u);
         win[j] = act[j] && own_free && rh[j] == i + 1u;
-        if (win[j] && !spec) {
+        if (win[j] && !xchg && !spec) {
           x[j] = ldcg(A + ii[j]);
           y[j] = ldcg(A + hh[j]);
         }
       }
       const uint64_t stpol = array_store_policy(a.flags);
+      if (xchg) {
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+          if (win[j]) y[j] = exch_hint(A + hh[j], x[j], stpol);
+      }
 #pragma unroll
       for (int j = 0; j < kU; ++j) {
         if (win[j]) {
           st_hint(A + ii[j], y[j], stpol);
-          st_hint(A + hh[j], x[j], stpol);
+          if (!xchg) st_hint(A + hh[j], x[j], stpol);
         }
       }
 #pragma unroll

@@ -52,6 +52,7 @@ pip_status pip_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options* 
   out->aux_bound_bytes = p.aux_bound;
   out->min_rounds = (n - 1 + p.F - 1) / p.F;
   out->driver = p.driver;
+  out->flags = p.flags;
   out->smem_bytes = p.smem_bytes;
   return PIP_OK;
 }

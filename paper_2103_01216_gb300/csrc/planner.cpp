@@ -329,9 +329,18 @@ pip_status make_plan(uint64_t n, pip_dtype dtype, double eps, const pip_options*
     if (ms > 0 && !o.wait_timeout_ns) tmo = (uint64_t)ms * 1000000ull;
   }
   p.timeout_ns = tmo;
-  // small prefixes are latency-bound: issue the array loads with the checks
-  // (measured 2-7 % faster up to F ~ 50K, 27 % slower at F ~ 1.1M)
-  if (p.F <= 131072u) p.flags |= PIP_FLAG_SPECULATE;
+  // Commit mode.  Small prefixes are latency-bound: issue both array loads
+  // with the checks (measured 2-7 % faster up to F ~ 50K, 27 % slower at
+  // F ~ 1.1M).  Large ones are bound by the rate of random accesses: the
+  // exchange commit does one random L2 transaction per swap instead of two.
+  // PIP_FLAG_SWAP_LOADSTORE / PIP_FLAG_SWAP_EXCHANGE force a mode.
+  if (o.flags & PIP_FLAG_SWAP_LOADSTORE) {
+    p.flags &= ~PIP_FLAG_SWAP_EXCHANGE;
+    if (p.F <= 131072u) p.flags |= PIP_FLAG_SPECULATE;
+  } else if (!(o.flags & PIP_FLAG_SWAP_EXCHANGE)) {
+    if (p.F <= 131072u) p.flags |= PIP_FLAG_SPECULATE;
+    else p.flags |= PIP_FLAG_SWAP_EXCHANGE;
+  }
   // whole-run limit: far above any legitimate run (about 1 us per round plus
   // 1 ns per element would already be slow), so only a defect can reach it
   uint64_t deadline = 60000000000ull + 2000ull * (p.n / p.F + 1) + 20ull * p.n;

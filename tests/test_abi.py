@@ -232,3 +232,16 @@ def test_device_entry_points_refuse_host_tensors(pip):
             call()
     assert torch.equal(a, torch.arange(64, dtype=torch.int64))
     assert bool((lists == -1).all()) and bool((trees == -1).all())
+
+
+def test_noalloc_refuses_host_memory_before_any_launch(pip):
+    # the no-allocation entry point is reached through the raw C ABI: it
+    # checks the pointer itself and leaves host memory untouched
+    import torch
+
+    a = torch.arange(64, dtype=torch.int64)
+    L = pip.lib()
+    assert L.pip_shuffle_noalloc(ctypes.c_void_p(a.data_ptr()), 64, pip.DTYPES["u64"], 1, 0.5, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle_noalloc(ctypes.c_void_p(a.data_ptr()), 64, pip.DTYPES["u64"], 1, 1.5, None) == pip.PIP_EINVAL
+    assert L.pip_shuffle_noalloc(ctypes.c_void_p(a.data_ptr()), 1, pip.DTYPES["u64"], 1, 0.5, None) == pip.PIP_OK
+    assert torch.equal(a, torch.arange(64, dtype=torch.int64))

@@ -4,10 +4,13 @@ configuration ``bench.py`` times (default plans).
 * n = 10^9 uint64, seed 2: the whole output for eps = 0.25, 0.5 and 0.75 is
   compared with one run of the sequential oracle (the permutation does not
   depend on eps).
-* n = 2^30 16-byte records, seed 3, eps = 0.5: the keys form a permutation and
-  every record keeps its payload (properties that hold at any size).
+* n = 2^30 16-byte records, seed 3, eps = 0.5: the whole output against one
+  run of the sequential oracle.
 * the 8192-array batch (sizes log-uniform in [2^8, 2^22], stream seed 7): every
   array against the oracle, computed by a process pool started with ``spawn``.
+* serving: the served workload's four largest requests (near 2^28 elements,
+  uint32 and uint64) with its first 16 requests, under the 120 GB budget,
+  each against the oracle.
 * scratch: with caller-provided scratch of exactly the planned size the
   device's free memory does not move, and the plan obeys the aux bound.
 * tree contraction of 2^25 leaves and list contraction of 2^26 nodes at
@@ -53,27 +56,33 @@ def test_headline_1e9_every_eps_equals_the_oracle(pip):
         torch.cuda.empty_cache()
 
 
-def test_records_2pow30_keep_keys_and_payloads(pip):
+def test_records_2pow30_equal_the_oracle(pip):
+    # the record configuration at its stated size (2^30 16-byte records,
+    # 16 GiB, seed 3, eps = 0.5, default plan): the whole output against one
+    # run of the sequential oracle on the same input, record by record
     torch = torch_cuda()
     n, seed = 1 << 30, 3
-    A = torch.empty((n, 2), dtype=torch.int64, device="cuda")
-    A[:, 0] = torch.arange(n, dtype=torch.int64, device="cuda")
-    # payloads from the workload generator, built on the host in chunks
+    host = np.empty((n, 2), dtype=np.uint64)
     chunk = 1 << 26
     for c0 in range(0, n, chunk):
         keys = np.arange(c0, min(n, c0 + chunk), dtype=np.uint64)
-        A[c0:c0 + keys.size, 1] = torch.from_numpy(workloads.record_payload(keys).view(np.int64)).cuda()
-    pip.shuffle(A, seed=seed, eps=0.5)
+        host[c0:c0 + keys.size, 0] = keys
+        host[c0:c0 + keys.size, 1] = workloads.record_payload(keys)
+    A = torch.from_numpy(host.view(np.int64)).cuda()
+    plan = pip.plan(n, "rec128", 0.5)
+    st = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    pip.shuffle(A, seed=seed, eps=0.5, stats=st)
     pip.check()
-    keys = A[:, 0]
-    seen = torch.zeros(n, dtype=torch.bool, device="cuda")
-    seen[keys] = True
-    assert bool(seen.all())
-    del seen
-    assert not torch.equal(keys[:1000], torch.arange(1000, dtype=torch.int64, device="cuda"))
+    s = pip.read_stats(st)
+    assert s.status == 0 and s.attempts == (n - 1) + s.losers
+    assert plan["driver"] == pip.DRIVER_GRID
+    got = A.cpu().numpy().view(np.uint64)
+    del A
+    torch.cuda.empty_cache()
+    assert not np.array_equal(got[:1000, 0], np.arange(1000, dtype=np.uint64))
+    oracle.knuth_hash(host, seed)  # in place: host becomes the expected output
     for c0 in range(0, n, chunk):
-        blk = A[c0:c0 + chunk].cpu().numpy().view(np.uint64)
-        assert np.array_equal(blk[:, 1], workloads.record_payload(blk[:, 0]))
+        assert np.array_equal(got[c0:c0 + chunk], host[c0:c0 + chunk]), c0
 
 
 def _oracle_slice(args):
@@ -129,6 +138,68 @@ def test_batch_8192_arrays_all_equal_the_oracle(pip):
         shm.unlink()
 
 
+def _oracle_request(args):
+    """Worker: the oracle's output of one served request (A[i] = i, seed =
+    request id) written into its slice of the shared buffer."""
+    shm_name, off, n, itemsize, seed = args
+    from multiprocessing import shared_memory
+
+    import oracle as orc
+
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        dt = np.uint32 if itemsize == 4 else np.uint64
+        a = np.ndarray((n,), dtype=dt, buffer=shm.buf, offset=off)
+        a[:] = np.arange(n, dtype=dt)
+        orc.knuth_hash(a, seed)
+    finally:
+        shm.close()
+    return n
+
+
+def test_served_largest_requests_equal_the_oracle(pip):
+    # the serving workload's largest requests (sizes near 2^28, both element
+    # types) served together with the stream's first 16 requests, under the
+    # 120 GB budget: every result against the oracle
+    from multiprocessing import shared_memory
+
+    sizes, dtypes, seeds, _ = workloads.serve_workload()
+    top = [int(j) for j in np.argsort(-sizes)[:4]]
+    ids = top + [j for j in range(16) if j not in top]
+    assert {dtypes[j] for j in top} == {"u32", "u64"}
+    item = {j: 4 if dtypes[j] == "u32" else 8 for j in ids}
+    offs, total = {}, 0
+    for j in ids:
+        offs[j] = total
+        total += (int(sizes[j]) * item[j] + 255) // 256 * 256
+    shm = shared_memory.SharedMemory(create=True, size=total)
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+            jobs = [(shm.name, offs[j], int(sizes[j]), item[j], int(seeds[j])) for j in ids]
+            async_res = pool.map_async(_oracle_request, jobs)
+            got = {}
+            with pip.Server(120 * 10**9) as srv:
+                tickets = {j: srv.submit(int(sizes[j]), str(dtypes[j]), seed=int(seeds[j]), eps=0.5) for j in ids}
+                for j, t in tickets.items():
+                    ptr, st = srv.wait(t)
+                    assert st.status == 0, j
+                    n = int(sizes[j])
+                    got[j] = pip.device_view(ptr, n, str(dtypes[j])).cpu().numpy().copy()
+                    assert st.attempts == (n - 1) + st.losers
+                    srv.release(t)
+                assert srv.info().status == 0
+            assert sum(async_res.get()) == int(sum(sizes[j] for j in ids))
+        for j in ids:
+            dt = np.uint32 if item[j] == 4 else np.uint64
+            want = np.ndarray((int(sizes[j]),), dtype=dt, buffer=shm.buf, offset=offs[j])
+            assert np.array_equal(got[j].view(dt), want), (j, int(sizes[j]), dtypes[j])
+            del want
+    finally:
+        shm.close()
+        shm.unlink()
+
+
 @pytest.mark.parametrize("eps", [0.25, 0.5, 0.75])
 def test_scratch_is_exactly_the_plan(pip, eps):
     torch = torch_cuda()
@@ -169,11 +240,14 @@ def test_tree_contraction_in_the_bench_launch_shape(pip):
     out = t.cpu().numpy().view(np.uint64).reshape(rec.shape)
     del t
     torch.cuda.empty_cache()
+    # schedule-free check first: every rake undone back to the input
+    rc, back = oracle.tree_uncontract(out, rec)
+    assert rc == 0 and np.array_equal(back, rec)
+    del back
+    # then the records under the schedule reading (F, kmax = 2.5 F + 2)
     want = rec.copy()
     oracle.tree_contract(want, F, F * 5 // 2 + 2)
     assert np.array_equal(out, want)
-    rc, back = oracle.tree_uncontract(out, rec)
-    assert rc == 0 and np.array_equal(back, rec)
 
 
 def test_list_contraction_one_long_list(pip):

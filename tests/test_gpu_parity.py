@@ -26,7 +26,10 @@ def pip():
 
 # the three round drivers: persistent grid, one block, one cluster (DSMEM tables),
 # and the first two under the two-reservation rule of Algorithm 1 as printed
-DRIVERS = {"grid": 32, "cta": 64, "cluster": 128, "grid_tworeserve": 32 | 512, "cta_tworeserve": 64 | 512}
+# and the grid driver under each commit mode (the exchange at L2, and plain
+# loads and stores) whatever the prefix size
+DRIVERS = {"grid": 32, "cta": 64, "cluster": 128, "grid_tworeserve": 32 | 512, "cta_tworeserve": 64 | 512,
+           "grid_exchange": 32 | 8, "grid_loadstore": 32 | 4, "grid_tworeserve_exchange": 32 | 512 | 8}
 
 
 def expect_hashed(arr, seed):
@@ -195,6 +198,29 @@ def test_output_does_not_depend_on_launch_shape(pip):
     for c in configs:
         out, _ = gpu_shuffle(pip, arr, seed=seed, eps=0.5, **c)
         assert np.array_equal(out, ref), c
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "rec128"])
+@pytest.mark.parametrize("mode", ["exchange", "loadstore", "speculate"])
+@pytest.mark.parametrize("n,F", [(100003, 977), ((1 << 20) + 5, 150000), (3 << 16, 4096)])
+def test_commit_modes_equal_the_oracle(pip, dtype, mode, n, F):
+    # every commit mode of the grid driver on every element size, at prefixes
+    # on both sides of the planner's switch between them
+    flags = DRIVERS["grid"] | {"exchange": 8, "loadstore": 4, "speculate": 256}[mode]
+    arr = workloads.make(n, dtype)
+    out, stats = gpu_shuffle(pip, arr, seed=n % 97, eps=0.5, fresh_per_round=F, with_stats=True, flags=flags)
+    assert np.array_equal(out, expect_hashed(arr, n % 97))
+    assert stats.status == 0 and stats.attempts == (n - 1) + stats.losers
+
+
+def test_planner_picks_the_commit_mode_by_prefix(pip):
+    small = pip.plan(10**9, "u64", 0.5)
+    large = pip.plan(10**9, "u64", 0.25)
+    assert small["driver"] == large["driver"] == pip.DRIVER_GRID
+    assert small["flags"] & 256 and not small["flags"] & 8
+    assert large["flags"] & 8 and not large["flags"] & 256
+    forced = pip.plan(10**9, "u64", 0.25, flags=4)
+    assert not forced["flags"] & 8
 
 
 def test_records_keep_their_payload(pip):
