@@ -291,13 +291,19 @@ def make_device_input(torch, n, dtype, device):
     return A
 
 
-def time_steps(torch, pip, A, seed, eps, steps, warmup, stream, opts):
+def time_steps(torch, pip, A, seed, eps, steps, warmup, stream, opts, flush=None):
+    """CUDA-event times of `steps` shuffles of A on `stream` after `warmup`
+    untimed ones.  `flush` (a CUDA tensor larger than L2) is rewritten
+    between timed steps, outside the timed region, for inputs that L2 holds."""
     for _ in range(warmup):
         pip.shuffle(A, seed=seed, eps=eps, stream=stream, **opts)
     pip.check(stream)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
     for s, e in evs:
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.add_(1)
         s.record(stream)
         pip.shuffle(A, seed=seed, eps=eps, stream=stream, **opts)
         e.record(stream)
@@ -306,37 +312,105 @@ def time_steps(torch, pip, A, seed, eps, steps, warmup, stream, opts):
     return [s.elapsed_time(e) for s, e in evs]
 
 
-def floor_ms(torch, pip, A, seed, stream, reps=3):
+def floor_ms(torch, pip, A, seed, stream, reps=3, mode=0):
     """Bare swap traffic of the same shuffle with no conflict resolution
-    (pip_calibrate_swap_floor): the practical floor of the round drivers."""
+    (pip_calibrate_swap_floor, which destroys A): the practical floor of the
+    round drivers, with the random side as an exchange (mode 0) or a load and
+    a store (mode 1)."""
     for _ in range(2):
-        pip.calibrate_swap_floor(A, seed=seed, stream=stream)
+        pip.calibrate_swap_floor(A, seed=seed, stream=stream, mode=mode)
     torch.cuda.synchronize()
     out = []
     for _ in range(reps):
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        pip.calibrate_swap_floor(A, seed=seed, stream=stream)
+        pip.calibrate_swap_floor(A, seed=seed, stream=stream, mode=mode)
         e.record(stream)
         e.synchronize()
         out.append(s.elapsed_time(e))
     return min(out)
 
 
-def run_batch(args):
-    """Batched workload: 8192 uint32 arrays A[i]=i, sizes log-uniform in
-    [2^8, 2^22] (stream seed 7), per-array seed = index, eps = 0.5.  One
-    launch (and its CUDA-graph replay) against one pip_shuffle per array."""
-    import numpy as np
+def cuda_runtime():
+    """A CUDA runtime library for the default memory pool's counters (the
+    pool is a driver object shared by every runtime in the process), or None."""
+    import ctypes
+    import ctypes.util
+    import glob
+
     import torch
 
-    import paper_2103_01216_gb300 as pip
-    import workloads
-    from paper_2103_01216_gb300 import _build
+    cands = [ctypes.util.find_library("cudart")]
+    for root in [os.path.dirname(torch.__file__), "/usr/local/cuda/lib64"]:
+        cands += sorted(glob.glob(os.path.join(root, "**", "libcudart.so*"), recursive=True))
+    for c in [c for c in cands if c]:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    return None
 
-    _build.build()
-    torch.cuda.set_device(0)
-    sizes, seeds = workloads.batch_workload(count=args.batch_count)
+
+def pool_bytes(rt, device):
+    """(reserved, used) bytes of the device's default memory pool."""
+    import ctypes
+
+    if rt is None:
+        return None
+    pool = ctypes.c_void_p()
+    if rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), device) != 0:
+        return None
+    out = []
+    for attr in (5, 7):  # cudaMemPoolAttrReservedMemCurrent, cudaMemPoolAttrUsedMemCurrent
+        v = ctypes.c_uint64()
+        if rt.cudaMemPoolGetAttribute(pool, attr, ctypes.byref(v)) != 0:
+            return None
+        out.append(v.value)
+    return tuple(out)
+
+
+def aux_accounting(torch, pip, A, n, dtype, seed, eps, stream):
+    """Scratch of one shuffle three ways: the plan's exact bytes against the
+    c * n^(1-eps) bound; what the stream-ordered pool holds and what
+    cudaMemGetInfo loses while a shuffle that allocates its own scratch runs;
+    and the cudaMemGetInfo delta of a shuffle given caller scratch of exactly
+    the planned size (the library then allocates nothing)."""
+    dev = torch.cuda.current_device()
+    rt = cuda_runtime()
+    p = pip.plan(n, dtype, eps)
+    torch.cuda.synchronize()
+    pool_before = pool_bytes(rt, dev)
+    free0, _ = torch.cuda.mem_get_info()
+    pip.shuffle(A, seed=seed, eps=eps, stream=stream)
+    free1, _ = torch.cuda.mem_get_info()
+    pool_during = pool_bytes(rt, dev)
+    pip.check(stream)
+    aux = torch.empty(max(256, p["aux_bytes"]), dtype=torch.uint8, device=A.device)
+    pip.shuffle(A, seed=seed, eps=eps, stream=stream, aux=aux)  # warm
+    pip.check(stream)
+    free2, _ = torch.cuda.mem_get_info()
+    pip.shuffle(A, seed=seed, eps=eps, stream=stream, aux=aux)
+    free3, _ = torch.cuda.mem_get_info()
+    pip.check(stream)
+    del aux
+    return {"plan_aux_bytes": p["aux_bytes"], "plan_smem_bytes": p["smem_bytes"],
+            "aux_bound_bytes": p["aux_bound_bytes"], "driver": p["driver"], "fresh_per_round": p["fresh_per_round"],
+            "pool_reserved_during": None if pool_during is None else pool_during[0] - pool_before[0],
+            "pool_used_during": None if pool_during is None else pool_during[1] - pool_before[1],
+            "mem_get_info_delta_pool": max(0, free0 - free1),
+            "mem_get_info_delta_caller_scratch": free2 - free3}
+
+
+def batch_case(torch, pip, count, steps, warmup, plain_steps, bopts):
+    """Batched workload: `count` uint32 arrays A[i]=i, sizes log-uniform in
+    [2^8, 2^22] (stream seed 7), per-array seed = index, eps = 0.5.  One
+    launch (and its CUDA-graph replay) against one pip_shuffle per array.
+    Returns the measurements as a dict."""
+    import numpy as np
+
+    import workloads
+
+    sizes, seeds = workloads.batch_workload(count=count)
     offs = np.zeros(len(sizes) + 1, dtype=np.int64)
     offs[1:] = np.cumsum((sizes + 3) // 4 * 4)  # 16-byte aligned arrays in one buffer
     buf = torch.empty(int(offs[-1]), dtype=torch.int32, device="cuda")
@@ -345,19 +419,12 @@ def run_batch(args):
         a.copy_(torch.arange(a.shape[0], dtype=torch.int32, device="cuda"))
     total = int(sizes.sum())
     eps = 0.5
-    bopts = {}
-    if args.block_threads:
-        bopts["block_threads"] = args.block_threads
-    if args.prefix_c:
-        bopts["prefix_c"] = args.prefix_c
-    if args.flags:
-        bopts["flags"] = args.flags
     b = pip.Batch(arrays, [int(x) for x in seeds], eps=eps, **bopts)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run()
     pip.check()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with ClockSampler(torch.cuda.current_device()) as clk:
         for s_, e_ in ev:
             s_.record(stream)
@@ -378,15 +445,16 @@ def run_batch(args):
     torch.cuda.synchronize()
     gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     gs.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         g.replay()
     ge.record()
     torch.cuda.synchronize()
     pip.check()
-    graph_ms = gs.elapsed_time(ge) / args.steps
+    graph_ms = gs.elapsed_time(ge) / steps
+    del g
     # plain path: one launch per array, FIFO on one stream
     plain_ms = []
-    for _ in range(args.plain_steps):
+    for _ in range(plain_steps):
         ps, pe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ps.record()
         for a, sd in zip(arrays, seeds):
@@ -394,8 +462,7 @@ def run_batch(args):
         pe.record()
         pip.check()
         plain_ms.append(ps.elapsed_time(pe))
-    # identical output: the batch and the plain path applied the same number of
-    # shuffles to every array; compare both against a fresh re-run pair
+    # identical output: a sample of arrays through both paths from A[i] = i
     chk = [j for j in range(0, len(sizes), max(1, len(sizes) // 64))]
     ref = [torch.arange(int(sizes[j]), dtype=torch.int32, device="cuda") for j in chk]
     bb = [torch.arange(int(sizes[j]), dtype=torch.int32, device="cuda") for j in chk]
@@ -406,31 +473,56 @@ def run_batch(args):
     identical = all(bool(torch.equal(x, y)) for x, y in zip(ref, bb))
     bms = sum(batched_ms) / len(batched_ms)
     pms = sum(plain_ms) / len(plain_ms) if plain_ms else float("nan")
+    out = {
+        "workload": f"batch_{len(sizes)}_u32_log_uniform_2^8_2^22_seed7_eps0.5", "arrays": len(sizes),
+        "total_elems": total, "fmax": b.plan.fmax, "block_threads": b.plan.block_threads,
+        "ms_per_step": bms, "value": total / (bms / 1e3), "unit": "elems/s",
+        "graph_ms_per_step": graph_ms, "graph_value": total / (graph_ms / 1e3),
+        "plain": {"ms_per_step": pms, "value": total / (pms / 1e3), "launches_per_step": len(sizes),
+                  "path": "pip_shuffle per array, FIFO on one stream"},
+        "speedup_vs_plain": pms / bms, "graph_speedup_vs_plain": pms / graph_ms,
+        "identical_output_sample": identical, "steps": steps, "warmup": warmup,
+        "clocks": clk.summary(), "step_ms": batched_ms,
+    }
+    del arrays, buf, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args):
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    bopts = {}
+    if args.block_threads:
+        bopts["block_threads"] = args.block_threads
+    if args.prefix_c:
+        bopts["prefix_c"] = args.prefix_c
+    if args.flags:
+        bopts["flags"] = args.flags
+    r = batch_case(torch, pip, args.batch_count, args.steps, args.warmup, args.plain_steps, bopts)
     line = {
         "metric": "shuffled elems/s (batched, 8192 arrays)",
-        "value": total / (bms / 1e3),
+        "value": r["value"],
         "unit": "elems/s",
         "n_gpus": 1,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": bms,
+        "ms_per_step": r["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": f"batch_{len(sizes)}_u32_log_uniform_2^8_2^22_seed7_eps0.5", "arrays": len(sizes),
-                   "total_elems": total, "fmax": b.plan.fmax, "block_threads": b.plan.block_threads,
-                   "l2": "inputs larger than L2 (no flush)"},
-        "graph_ms_per_step": graph_ms,
-        "graph_value": total / (graph_ms / 1e3),
-        "plain": {"ms_per_step": pms, "value": total / (pms / 1e3), "launches_per_step": len(sizes),
-                  "path": "pip_shuffle per array, FIFO on one stream"},
-        "speedup_vs_plain": pms / bms,
-        "identical_output_sample": identical,
+        "config": {"workload": r["workload"], "arrays": r["arrays"], "total_elems": r["total_elems"],
+                   "fmax": r["fmax"], "block_threads": r["block_threads"], "l2": "inputs larger than L2 (no flush)"},
+        **{k: r[k] for k in ("graph_ms_per_step", "graph_value", "plain", "speedup_vs_plain",
+                             "graph_speedup_vs_plain", "identical_output_sample", "clocks", "step_ms")},
         "gpu_launches": args.steps,
-        "clocks": clk.summary(),
-        "step_ms": batched_ms,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -448,9 +540,11 @@ def run_floor(args):
     torch.cuda.set_device(0)
     A = make_device_input(torch, args.n, args.dtype, "cuda")
     stream = torch.cuda.current_stream()
-    f = floor_ms(torch, pip, A, args.seed, stream, reps=max(1, args.steps))
+    f = floor_ms(torch, pip, A, args.seed, stream, reps=max(1, args.steps), mode=pip.FLOOR_EXCHANGE)
+    fl = floor_ms(torch, pip, A, args.seed, stream, reps=max(1, args.steps), mode=pip.FLOOR_LOADSTORE)
     print(json.dumps({"metric": "bare swap floor", "value": args.n / (f / 1e3), "unit": "swaps/s", "ms": f,
-                      "n": args.n, "dtype": args.dtype, "bytes_algorithmic_per_swap": BYTES_PER_ELEM[args.dtype]}),
+                      "loadstore_ms": fl, "n": args.n, "dtype": args.dtype,
+                      "bytes_algorithmic_per_swap": BYTES_PER_ELEM[args.dtype]}),
           flush=True)
     return 0
 
@@ -730,44 +824,40 @@ def _percentile(xs, q):
     return xs[k]
 
 
-def run_serve(args):
-    """Served workload: requests with sizes log-uniform in [2^12, 2^28]
-    (stream 5), uint32/uint64 by a seeded coin, seed = request id, eps = 0.5,
-    120 GB device budget.  Closed loop first (saturation throughput), then
-    Poisson arrivals at 80% of it; the same schedule through the plain
-    FIFO path (allocate, initialise, pip_shuffle, synchronize, one at a time)."""
+def serve_case(torch, pip, N, opts, plain_N, plain_open=False):
+    """Served workload: the first N of the 20,000-request stream -- sizes
+    log-uniform in [2^12, 2^28] (stream 5), uint32/uint64 by a seeded coin,
+    seed = request id, eps = 0.5 -- under a 120 GB device budget.  Closed
+    loop first (saturation throughput), then Poisson arrivals at 80 % of it.
+    The plain FIFO path (allocate, initialise, pip_shuffle, synchronize, one
+    request at a time) runs back to back over the first plain_N requests of
+    the same stream (its saturation), and with plain_open also on their
+    arrival schedule.  Throughputs are compared per element, since the
+    plain path's prefix has its own size mix."""
     import threading as th
 
-    import numpy as np
-    import torch
-
-    import paper_2103_01216_gb300 as pip
     import workloads
-    from paper_2103_01216_gb300 import _build
 
-    _build.build()
-    torch.cuda.set_device(0)
-    N = args.requests
-    sizes, dtypes, seeds, _ = workloads.serve_workload(count=20000)
-    sizes, dtypes, seeds = sizes[:N], dtypes[:N], seeds[:N]
+    sizes_all, dtypes_all, seeds_all, _ = workloads.serve_workload(count=20000)
+    sizes, dtypes, seeds = sizes_all[:N], dtypes_all[:N], seeds_all[:N]
     total = int(sizes.sum())
     budget = 120 * 10**9
     eps = 0.5
-    opts = dict(rounds_per_tick=args.rounds_per_tick, fresh_cap=args.fresh_cap, tick_us=args.tick_us)
 
-    def closed_loop():
+    def closed_loop(k):
         with pip.Server(budget, **opts) as srv:
             t0 = time.perf_counter()
-            for n, d, s in zip(sizes, dtypes, seeds):
-                srv.submit(int(n), str(d), seed=int(s), eps=eps)
-            for _ in range(N):  # release each request as soon as it finishes
+            for n, d, sd in zip(sizes[:k], dtypes[:k], seeds[:k]):
+                srv.submit(int(n), str(d), seed=int(sd), eps=eps)
+            for _ in range(k):  # release each request as soon as it finishes
                 srv.release(srv.next_done())
             dt = time.perf_counter() - t0
             info = srv.info()
         return dt, info
 
-    closed_loop()  # warm-up (kernel attributes, pools)
-    t_sat, info_sat = closed_loop()
+    closed_loop(min(N, 200))  # warm-up (kernel attributes, pools)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_sat, info_sat = closed_loop(N)
     rate = 0.8 * N / t_sat
     _, _, _, arrivals = workloads.serve_workload(count=20000, rate_per_s=rate)
     arrivals = arrivals[:N]
@@ -798,56 +888,73 @@ def run_serve(args):
         served_span = (max(done_at) - start_ns) / 1e9
         info = srv.info()
 
-    if args.no_plain:
-        print(json.dumps({"served_saturation_req_s": N / t_sat, "saturation_elems_s": total / t_sat,
-                          "p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99),
-                          "throughput_req_s": N / served_span, "ticks": info.ticks, **opts}), flush=True)
-        return 0
-    # plain FIFO path, same arrivals
-    plain_lat = []
-    t0 = time.perf_counter()
-    for j in range(N):
-        delay = arrivals[j] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        n = int(sizes[j])
-        A = torch.arange(n, dtype=torch.int64 if dtypes[j] == "u64" else torch.int32, device="cuda")
-        pip.shuffle(A, seed=int(seeds[j]), eps=eps)
-        torch.cuda.synchronize()
-        plain_lat.append((time.perf_counter() - t0 - arrivals[j]) * 1e3)
-        del A
-    plain_span = time.perf_counter() - t0
-    # plain closed loop (back to back)
-    t1 = time.perf_counter()
-    for j in range(N):
-        n = int(sizes[j])
-        A = torch.arange(n, dtype=torch.int64 if dtypes[j] == "u64" else torch.int32, device="cuda")
-        pip.shuffle(A, seed=int(seeds[j]), eps=eps)
+    def plain_one(j):
+        n = int(sizes_all[j])
+        A = torch.arange(n, dtype=torch.int64 if dtypes_all[j] == "u64" else torch.int32, device="cuda")
+        pip.shuffle(A, seed=int(seeds_all[j]), eps=eps)
         torch.cuda.synchronize()
         del A
-    plain_sat = time.perf_counter() - t1
+
+    plain = {"requests": plain_N, "path": "allocate, initialise, pip_shuffle, synchronize; one request at a time"}
+    if plain_N > 0:
+        plain_total = int(sizes_all[:plain_N].sum())
+        t1 = time.perf_counter()
+        for j in range(plain_N):
+            plain_one(j)
+        plain_sat = time.perf_counter() - t1
+        plain.update({"total_elems": plain_total, "saturation_req_s": plain_N / plain_sat,
+                      "saturation_elems_s": plain_total / plain_sat})
+        if plain_open:
+            plain_lat = []
+            t0 = time.perf_counter()
+            for j in range(plain_N):
+                delay = arrivals[j] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                plain_one(j)
+                plain_lat.append((time.perf_counter() - t0 - arrivals[j]) * 1e3)
+            plain.update({"p50_ms": _percentile(plain_lat, 50), "p99_ms": _percentile(plain_lat, 99),
+                          "throughput_req_s": plain_N / (time.perf_counter() - t0)})
+        torch.cuda.empty_cache()
+    served = {"requests": N, "total_elems": total, "p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99),
+              "throughput_req_s": N / served_span, "elems_s": total / served_span,
+              "saturation_req_s": N / t_sat, "saturation_elems_s": total / t_sat,
+              "arrival_rate_per_s": rate, "peak_used_bytes": info.peak_used_bytes, "ticks": info.ticks,
+              "big_lane_requests": getattr(info, "big_admitted", None), "clocks": clk.summary()}
+    out = {"workload": f"serve_{N}_of_20000_requests_log_uniform_2^12_2^28_u32_u64_eps0.5_budget120GB",
+           "served": served, "plain_fifo": plain, "options": dict(opts)}
+    if plain.get("saturation_elems_s"):
+        out["speedup_saturation_elems"] = served["saturation_elems_s"] / plain["saturation_elems_s"]
+    return out
+
+
+def run_serve(args):
+    import torch
+
+    import paper_2103_01216_gb300 as pip
+    from paper_2103_01216_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    opts = dict(rounds_per_tick=args.rounds_per_tick, fresh_cap=args.fresh_cap, tick_us=args.tick_us)
+    N = args.requests
+    r = serve_case(torch, pip, N, opts, 0 if args.no_plain else min(N, args.plain_requests),
+                   plain_open=not args.no_plain)
     line = {
         "metric": "served requests/s and p50/p99 latency vs FIFO plain path",
-        "value": N / served_span,
+        "value": r["served"]["throughput_req_s"],
         "unit": "requests/s",
         "n_gpus": 1,
         "steps": 1,
         "warmup": 1,
-        "ms_per_step": served_span * 1e3,
+        "ms_per_step": r["served"]["requests"] / r["served"]["throughput_req_s"] * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "u32/u64",
         "data": "synthetic",
-        "config": {"workload": f"serve_{N}_of_20000_requests_log_uniform_2^12_2^28_eps0.5_budget120GB",
-                   "requests": N, "total_elems": total, "arrival_rate_per_s": rate, **opts},
-        "served": {"p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99), "throughput_req_s": N / served_span,
-                   "elems_s": total / served_span, "saturation_req_s": N / t_sat, "saturation_elems_s": total / t_sat,
-                   "peak_used_bytes": info.peak_used_bytes, "ticks": info.ticks},
-        "plain_fifo": {"p50_ms": _percentile(plain_lat, 50), "p99_ms": _percentile(plain_lat, 99),
-                       "throughput_req_s": N / plain_span, "elems_s": total / plain_span,
-                       "saturation_req_s": N / plain_sat, "saturation_elems_s": total / plain_sat},
-        "speedup_saturation": plain_sat / t_sat,
+        "config": {"workload": r["workload"], "requests": N, **opts},
+        **{k: v for k, v in r.items() if k not in ("workload",)},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -877,7 +984,9 @@ def main():
                     choices=["single", "batch", "serve", "floor", "list", "tree", "scan"])
     ap.add_argument("--batch-count", type=int, default=8192)
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--plain-requests", type=int, default=2000,
+                    help="serve: requests of the stream's prefix timed through the plain FIFO path")
     ap.add_argument("--rounds-per-tick", type=int, default=0)
     ap.add_argument("--tick-us", type=int, default=0)
     ap.add_argument("--fresh-cap", type=int, default=1024)
@@ -885,6 +994,8 @@ def main():
     ap.add_argument("--no-rules", dest="rules", action="store_false",
                     help="skip the two-reservation rule ablation step")
     ap.add_argument("--no-plain", action="store_true", help="serve: skip the plain FIFO comparison")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="single workload: skip the other configurations (records, batch, serving, 2^20)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -947,7 +1058,6 @@ def main():
     torch.cuda.synchronize()
 
     # device-resident timing, with clocks sampled during the timed region
-    free_before, _ = torch.cuda.mem_get_info()
     with ClockSampler(torch.cuda.current_device()) as clk:
         if dist is not None:
             dist.barrier()
@@ -959,13 +1069,9 @@ def main():
     ms_per_step = total_ms / args.steps
     value = replica_throughput(n, world, args.steps, total_ms)
 
-    # aux bytes as seen by the allocator while a shuffle is in flight
-    side = torch.cuda.Stream()
-    with torch.cuda.stream(side):
-        pip.shuffle(A, seed=seed, eps=eps, stream=side, **opts)
-        free_during, _ = torch.cuda.mem_get_info()
-    pip.check(side)
-    aux_delta = max(0, free_before - free_during)
+    # scratch accounting: the plan, the stream-ordered pool while a shuffle
+    # runs, and caller-provided scratch (where nothing is allocated)
+    aux = {str(eps): aux_accounting(torch, pip, A, n, dtype, seed, eps, stream)}
 
     # stats of one run
     st_buf = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device=device)
@@ -976,11 +1082,12 @@ def main():
     # end to end through the host-memory entry point (pip_shuffle_host_stream):
     # every step copies its input from pinned host memory to the device,
     # shuffles it and copies the result back to pinned host memory; the
-    # copies of one step overlap the shuffles of its neighbours
+    # copies of one step overlap the shuffles of its neighbours.  The copy
+    # stages are then timed alone on the same buffers.
     e2e = None
     if args.e2e_steps > 0:
         host = A.cpu().pin_memory()
-        out = torch.empty_like(host).pin_memory()
+        out = torch.empty(host.shape, dtype=host.dtype, pin_memory=True)
         nbytes = host.numel() * host.element_size()
         slot = (nbytes + 255) // 256 * 256
         buf = torch.empty(3 * slot, dtype=torch.uint8, device=device)
@@ -995,13 +1102,49 @@ def main():
         e.record()
         pip.check()
         e2e_ms = max_over_ranks(s.elapsed_time(e), dist, device)
-        e2e = {"value": replica_throughput(n, world, args.e2e_steps, e2e_ms), "unit": "elems/s",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": e2e_ms / args.e2e_steps,
-               "api": "pip_shuffle_host_stream (pinned host buffers, copies overlapped with neighbouring shuffles)"}
-        del host, out, buf
+        hv, ov = host.view(-1).view(torch.uint8), out.view(-1).view(torch.uint8)
+        d0, d1 = buf[:nbytes], buf[slot:slot + nbytes]
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
 
-    # eps sweep (one timed step each, one warm-up)
+        def stage(fn):
+            torch.cuda.synchronize()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            fn()
+            b_.record()
+            torch.cuda.synchronize()
+            return a_.elapsed_time(b_)
+
+        def h2d():
+            with torch.cuda.stream(s1):
+                d0.copy_(hv, non_blocking=True)
+            torch.cuda.current_stream().wait_stream(s1)
+
+        def d2h():
+            with torch.cuda.stream(s2):
+                ov.copy_(d1, non_blocking=True)
+            torch.cuda.current_stream().wait_stream(s2)
+
+        def both():
+            h2d()
+            d2h()
+
+        h2d_ms, d2h_ms, both_ms = stage(h2d), stage(d2h), stage(both)
+        k = args.e2e_steps
+        model = (h2d_ms + d2h_ms + k * max(ms_per_step, both_ms)) / k
+        e2e = {"value": replica_throughput(n, world, k, e2e_ms), "unit": "elems/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "ms_per_step": e2e_ms / k, "steps": k,
+               "api": "pip_shuffle_host_stream (pinned host buffers, copies overlapped with neighbouring shuffles)",
+               "stages": {"h2d_ms": h2d_ms, "d2h_ms": d2h_ms, "h2d_and_d2h_together_ms": both_ms,
+                          "shuffle_ms": ms_per_step, "h2d_GB_s": nbytes / h2d_ms / 1e6,
+                          "d2h_GB_s": nbytes / d2h_ms / 1e6,
+                          "model_ms_per_step": model,
+                          "model": "(h2d + d2h + steps * max(shuffle, h2d and d2h together)) / steps: "
+                                   "the first copy in and the last copy out are not overlapped"}}
+        del host, out, buf, hv, ov, d0, d1
+
+    # eps sweep (one timed step each, one warm-up) and its scratch accounting
     sweep = {}
     for tok in [t for t in args.sweep.split(",") if t.strip()]:
         e_ = float(tok)
@@ -1010,8 +1153,10 @@ def main():
         t_s = ms_[0] / 1e3
         ach = BYTES_PER_ELEM[dtype] * n / t_s / 1e9
         sweep[str(e_)] = {"value": n / t_s, "unit": "elems/s", "ms": ms_[0], "fresh_per_round": p_["fresh_per_round"],
-                          "aux_bytes": p_["aux_bytes"], "aux_bound_bytes": p_["aux_bound_bytes"],
-                          "roofline_frac": ach / measured_peak_hbm()[0]}
+                          "driver": p_["driver"], "aux_bytes": p_["aux_bytes"], "smem_bytes": p_["smem_bytes"],
+                          "aux_bound_bytes": p_["aux_bound_bytes"], "roofline_frac": ach / measured_peak_hbm()[0]}
+        if ms_[0] < 1000.0:
+            aux[str(e_)] = aux_accounting(torch, pip, A, n, dtype, seed, e_, stream)
 
     # reservation-rule ablation (Algorithm 1 as printed: two reservations per
     # step, against the one-reservation rule of the default path), one step
@@ -1029,12 +1174,33 @@ def main():
                  "one_reservation": {"ms": ms_per_step, "value": value, "rounds": st.rounds,
                                      "loser_fraction": st.losers / max(1, st.attempts)}}
 
-    # bare swap traffic of the same shuffle (scrambles A; nothing reads it after)
+    # commit-mode ablation: the planner's mode against the other one, one step
+    modes = None
+    if args.rules:
+        other = pip.FLAG_SWAP_LOADSTORE if plan["flags"] & pip.FLAG_SWAP_EXCHANGE else pip.FLAG_SWAP_EXCHANGE
+        o3 = dict(opts)
+        o3["flags"] = o3.get("flags", 0) | other
+        ms3 = time_steps(torch, pip, A, seed, eps, 1, 1, stream, o3)
+        name = lambda f: "exchange" if f & pip.FLAG_SWAP_EXCHANGE else "loadstore"  # noqa: E731
+        modes = {"planned": name(plan["flags"]), name(plan["flags"]): ms_per_step,
+                 name(pip.plan(n, dtype, eps, **o3)["flags"]): ms3[0]}
+
+    # bare swap traffic of the same shuffle (destroys A; nothing reads it after)
     floor = None
     if not args.no_floor:
-        f_ms = floor_ms(torch, pip, A, seed, stream)
-        floor = {"ms": f_ms, "elems_s": n / (f_ms / 1e3), "frac_of_floor": f_ms / ms_per_step,
-                 "what": "pip_calibrate_swap_floor: the n-1 swaps with no conflict resolution"}
+        f_x = floor_ms(torch, pip, A, seed, stream, mode=pip.FLOOR_EXCHANGE)
+        f_l = floor_ms(torch, pip, A, seed, stream, mode=pip.FLOOR_LOADSTORE)
+        floor = {"ms": f_x, "elems_s": n / (f_x / 1e3), "frac_of_floor": f_x / ms_per_step,
+                 "loadstore_ms": f_l, "frac_of_loadstore_floor": f_l / ms_per_step,
+                 "what": "pip_calibrate_swap_floor: the n-1 swaps with no conflict resolution; ms with the "
+                         "random side as one exchange at L2, loadstore_ms as a load and a store"}
+    del A
+    torch.cuda.empty_cache()
+
+    # the other configurations of the workload set, one GPU only
+    configs = None
+    if args.configs and world == 1:
+        configs = run_configs(torch, pip, args, stream)
 
     if rank != 0:
         if dist is not None:
@@ -1073,19 +1239,80 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clocks,
         "plan": {k: plan[k] for k in ("driver", "fresh_per_round", "max_active", "slots", "grid_blocks",
-                                      "block_threads", "aux_bytes", "smem_bytes", "aux_bound_bytes", "min_rounds")},
-        "aux_alloc_delta_bytes": aux_delta,
+                                      "block_threads", "aux_bytes", "smem_bytes", "aux_bound_bytes", "min_rounds",
+                                      "flags")},
+        "aux": aux,
         "rounds": st.rounds,
         "loser_fraction": st.losers / max(1, st.attempts),
         "eps_sweep": sweep,
         "reservation_rules": rules,
+        "commit_modes": modes,
         "random_swap_floor": floor,
+        "configs": configs,
         "step_ms": ms,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_configs(torch, pip, args, stream):
+    """The rest of the workload set, each at its stated size, in this process:
+    the 2^20 shuffle (L2-resident, so L2 is flushed between timed steps), the
+    2^30 16-byte records, the 8192-array batch and the 20,000-request serving
+    stream."""
+    out = {}
+    peak = measured_peak_hbm()[0]
+    # configuration 1: n = 2^20 uint64, seed 1, eps = 0.5
+    n1 = 1 << 20
+    A1 = torch.arange(n1, dtype=torch.int64, device="cuda")
+    flush = torch.zeros(256 << 20, dtype=torch.int32, device="cuda")  # 1 GiB, larger than L2
+    p1 = pip.plan(n1, "u64", 0.5)
+    ms1 = time_steps(torch, pip, A1, 1, 0.5, max(args.steps, 10), args.warmup, stream, {}, flush=flush)
+    st1 = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    pip.shuffle(A1, seed=1, eps=0.5, stats=st1)
+    pip.check()
+    s1 = pip.read_stats(st1)
+    m1 = statistics.median(ms1)
+    out["shuffle_2^20_u64_seed1_eps0.5"] = {
+        "ms": m1, "value": n1 / (m1 / 1e3), "unit": "elems/s", "driver": p1["driver"],
+        "fresh_per_round": p1["fresh_per_round"], "rounds": s1.rounds, "steps": len(ms1),
+        "l2": "8 MiB input held by L2: a 1 GiB buffer is rewritten between timed steps",
+        "note": "round-latency-bound (about n / F rounds of a few microseconds); not an HBM case"}
+    del A1, flush
+    torch.cuda.empty_cache()
+
+    # configuration 3: n = 2^30 16-byte records, seed 3, eps = 0.5
+    n3 = 1 << 30
+    A3 = make_device_input(torch, n3, "rec128", "cuda")
+    p3 = pip.plan(n3, "rec128", 0.5)
+    k3 = min(args.steps, 5)
+    ms3 = time_steps(torch, pip, A3, 3, 0.5, k3, min(args.warmup, 3), stream, {})
+    st3 = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    pip.shuffle(A3, seed=3, eps=0.5, stats=st3)
+    pip.check()
+    s3 = pip.read_stats(st3)
+    m3 = sum(ms3) / len(ms3)
+    f3 = floor_ms(torch, pip, A3, 3, stream, mode=pip.FLOOR_EXCHANGE)
+    f3l = floor_ms(torch, pip, A3, 3, stream, mode=pip.FLOOR_LOADSTORE)
+    ach3 = BYTES_PER_ELEM["rec128"] * n3 / (m3 / 1e3) / 1e9
+    out["records_2^30_rec128_seed3_eps0.5"] = {
+        "ms": m3, "value": n3 / (m3 / 1e3), "unit": "elems/s", "driver": p3["driver"],
+        "fresh_per_round": p3["fresh_per_round"], "rounds": s3.rounds, "steps": k3, "step_ms": ms3,
+        "roofline": {"bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s", "frac": ach3 / peak,
+                     "algorithmic_bytes_per_elem": BYTES_PER_ELEM["rec128"]},
+        "random_swap_floor": {"ms": f3, "loadstore_ms": f3l, "frac_of_floor": f3 / m3},
+        "aux_bytes": p3["aux_bytes"], "aux_bound_bytes": p3["aux_bound_bytes"]}
+    del A3
+    torch.cuda.empty_cache()
+
+    # configuration 4: the 8192-array batch
+    out["batch_8192_u32"] = batch_case(torch, pip, 8192, min(args.steps, 5), min(args.warmup, 3), 1, {})
+    # configuration 5: the serving stream
+    if args.requests > 0:
+        out["serve"] = serve_case(torch, pip, args.requests, {}, min(args.requests, args.plain_requests))
+    return out
 
 
 if __name__ == "__main__":

@@ -411,15 +411,23 @@ pip_status pip_shuffle_noalloc(void *A_dev, uint64_t n, pip_dtype dtype, uint64_
                                double eps, void *stream);
 
 /*
- * pip_calibrate_swap_floor -- measurement probe, not a shuffle.  The paper has
- * no counterpart; it is a tool for reading the round drivers' speed.
+ * pip_calibrate_swap_floor -- BENCHMARK-ONLY PROBE THAT DESTROYS ITS INPUT; not
+ * a shuffle.  The paper has no counterpart; it is a tool for reading the round
+ * drivers' speed and has no use in a program that wants its data.
  *   Performs the n-1 swaps A[i] <-> A[H[i]] (hashed targets of `seed`) all at
  *   once with no conflict resolution, so A ends up with unspecified content
  *   (its elements may be duplicated or lost).  Times taken around it give the
  *   cost of the bare data movement of a shuffle on this GPU: coalesced i-side
- *   accesses plus one random element read and write per swap.
+ *   accesses plus one random element access per swap, done as the round
+ *   drivers' commit modes do it: mode PIP_FLOOR_EXCHANGE (0) exchanges A[i]
+ *   into A[H[i]] with one atomic at L2 and stores the returned element at
+ *   A[i]; mode PIP_FLOOR_LOADSTORE (1) loads both elements and stores both.
+ *   Other modes return PIP_EINVAL.
  */
-pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed, void *stream);
+#define PIP_FLOOR_EXCHANGE 0
+#define PIP_FLOOR_LOADSTORE 1
+pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, uint64_t seed, int mode,
+                                    void *stream);
 
 /*
  * pip_shuffle_host_stream -- shuffles `count` arrays held in host memory, in

@@ -236,7 +236,7 @@ def lib() -> ctypes.CDLL:
         L.pip_shuffle_host_stream.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(u64),
                                               ctypes.c_uint32, u64, i32, dbl, vp, u64, vp]
         L.pip_shuffle_host_stream.restype = i32
-        L.pip_calibrate_swap_floor.argtypes = [vp, u64, i32, u64, vp]
+        L.pip_calibrate_swap_floor.argtypes = [vp, u64, i32, u64, i32, vp]
         L.pip_calibrate_swap_floor.restype = i32
         L.pip_serve_create.argtypes = [ctypes.POINTER(vp), u64, i32, ctypes.POINTER(ServeOptions)]
         L.pip_serve_create.restype = i32
@@ -581,11 +581,18 @@ class Server:
         return False
 
 
-def calibrate_swap_floor(A, seed: int = 0, stream=None) -> None:
-    """Measurement probe (``pip_calibrate_swap_floor``): the bare swap traffic of
-    a shuffle of ``A`` with no conflict resolution; leaves ``A`` unspecified."""
-    _raise(lib().pip_calibrate_swap_floor(A.data_ptr(), A.shape[0], tensor_dtype(A), seed, _stream_handle(stream)),
-           "pip_calibrate_swap_floor")
+FLOOR_EXCHANGE, FLOOR_LOADSTORE = 0, 1
+
+
+def calibrate_swap_floor(A, seed: int = 0, stream=None, mode: int = FLOOR_EXCHANGE) -> None:
+    """Benchmark-only probe that destroys ``A`` (``pip_calibrate_swap_floor``):
+    the bare swap traffic of a shuffle of ``A`` with no conflict resolution
+    (A's content afterwards is unspecified).  ``mode``: FLOOR_EXCHANGE (the
+    random side as one atomic exchange at L2) or FLOOR_LOADSTORE."""
+    if not A.is_cuda or not A.is_contiguous():
+        raise ValueError("A must be a contiguous CUDA tensor")
+    _raise(lib().pip_calibrate_swap_floor(A.data_ptr(), A.shape[0], tensor_dtype(A), seed, int(mode),
+                                          _stream_handle(stream)), "pip_calibrate_swap_floor")
 
 
 # ------------------------------------------------------------------ list contraction
