@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_list_check.restype = ctypes.c_int
             L.oracle_list_nearest_larger.argtypes = [vp, u64, vp]
             L.oracle_list_nearest_larger.restype = ctypes.c_int
+            L.oracle_list_rank.argtypes = [vp, u64, vp]
+            L.oracle_list_rank.restype = ctypes.c_int
             L.oracle_tree_contract.argtypes = [vp, u64, u64, u64]
             L.oracle_tree_contract.restype = ctypes.c_int64
             L.oracle_tree_contract_seq.argtypes = [vp, u64]
@@ -185,6 +187,18 @@ def list_nearest_larger(rec: np.ndarray) -> np.ndarray:
     out = np.empty_like(rec)
     if lib().oracle_list_nearest_larger(rec.ctypes.data, rec.shape[0], out.ctypes.data) != 0:
         raise MemoryError("oracle_list_nearest_larger")
+    return out
+
+
+def list_rank(rec: np.ndarray) -> np.ndarray:
+    """List ranking by definition (Section 4.2: the value list contraction and
+    its reconstruction step compute): for every node, the number of nodes
+    before it and after it in its list, as an (n, 2) uint64 array.  ``rec``
+    must hold valid acyclic lists (:func:`list_check`)."""
+    rec = _records(rec)
+    out = np.empty_like(rec)
+    if lib().oracle_list_rank(rec.ctypes.data, rec.shape[0], out.ctypes.data) != 0:
+        raise ValueError("a list is longer than n (a cycle)")
     return out
 
 

@@ -26,6 +26,12 @@
  * the neighbours at contraction are the nearest nodes with a larger index on
  * each side in the original list order (all smaller nodes are gone by then),
  * computed with the classic stack scan for nearest larger values.
+ *
+ * List ranking (Section 4.2: list contraction followed by the reconstruction
+ * step that distributes the values back down the contraction tree) returns
+ * for each node its position in its list.  Its output is unique, so the
+ * oracle is the plain definition: walk every list from its head and count,
+ * from the head and from the tail.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -100,5 +106,25 @@ ORACLE_API int oracle_list_nearest_larger(const uint64_t *rec, uint64_t n, uint6
         }
     }
     free(stack);
+    return 0;
+}
+
+/* List ranking by its definition: out[2i] = the number of nodes before node
+ * i in its list, out[2i+1] = the number of nodes after it.  rec must pass
+ * oracle_list_check (the walk stops at n steps otherwise).  Returns 0, or -1
+ * when a list is longer than n (a cycle). */
+ORACLE_API int oracle_list_rank(const uint64_t *rec, uint64_t n, uint64_t *out)
+{
+    for (uint64_t h = 0; h < n; ++h) {
+        if (rec[2 * h] != ORACLE_NIL) continue;   /* not a head */
+        uint64_t len = 0;
+        for (uint64_t v = h; v != ORACLE_NIL; v = rec[2 * v + 1]) {
+            if (len >= n) return -1;
+            out[2 * v] = len;                     /* nodes before v */
+            ++len;
+        }
+        for (uint64_t v = h; v != ORACLE_NIL; v = rec[2 * v + 1])
+            out[2 * v + 1] = len - 1 - out[2 * v];  /* nodes after v */
+    }
     return 0;
 }

@@ -122,3 +122,53 @@ def test_checker_rejects_broken_lists():
     cyc = workloads.lists_from_order(np.arange(10, dtype=np.uint64))
     cyc[0, 0], cyc[9, 1] = 9, 0
     assert oracle.list_check(cyc) != 0
+
+
+# ------------------------------------------------------------------ list ranking
+@pytest.mark.parametrize("n,nlists", [(1, 1), (2, 1), (17, 1), (1000, 7), (100003, 1), (100003, 64)])
+def test_list_rank_equals_the_visiting_order(n, nlists):
+    # the generator visits order[] in turn, cut into near-equal lists: the
+    # k-th node of a list has k nodes before it and (length - 1 - k) after it
+    order = np.random.default_rng(n + nlists).permutation(n).astype(np.uint64)
+    rec = workloads.lists_from_order(order, nlists)
+    out = oracle.list_rank(rec)
+    cuts = np.linspace(0, n, max(1, min(nlists, n)) + 1).astype(np.int64)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        seg = order[a:b].astype(np.int64)
+        k = np.arange(b - a, dtype=np.uint64)
+        assert np.array_equal(out[seg, 0], k)
+        assert np.array_equal(out[seg, 1], (b - a - 1) - k)
+
+
+def test_list_rank_follows_the_contraction_tree():
+    # the relation the reconstruction step uses (Section 4.2): with p the
+    # nearest larger node on v's left (the neighbour v had when spliced out),
+    # rank(v) = rank(p) + d where d - 1 nodes lie between them, all of them
+    # smaller than v (they were spliced out before v); likewise on the right
+    order = np.random.default_rng(3).permutation(3000).astype(np.uint64)
+    rec = workloads.lists_from_order(order, 3)
+    rank = oracle.list_rank(rec)
+    nl = oracle.list_nearest_larger(rec)
+    where = np.empty(3000, dtype=np.int64)
+    where[order.astype(np.int64)] = np.arange(3000)
+    for v in range(3000):
+        p, q = int(nl[v, 0]), int(nl[v, 1])
+        if p != NIL:
+            d = int(rank[v, 0]) - int(rank[p, 0])
+            assert d >= 1 and where[v] - where[p] == d
+            assert all(int(order[j]) < v for j in range(where[p] + 1, where[v]))
+        else:  # no larger node before v: all nodes before it are smaller
+            assert all(int(order[j]) < v for j in range(where[v] - int(rank[v, 0]), where[v]))
+        if q != NIL:
+            d = int(rank[v, 1]) - int(rank[q, 1])
+            assert d >= 1 and where[q] - where[v] == d
+            assert all(int(order[j]) < v for j in range(where[v] + 1, where[q]))
+
+
+def test_list_rank_rejects_a_cycle():
+    rec = workloads.random_lists(10, rng_seed=1)
+    head = int(np.nonzero(rec[:, 0] == NIL)[0][0])
+    tail = int(np.nonzero(rec[:, 1] == NIL)[0][0])
+    rec[head, 0], rec[tail, 1] = tail, head  # close the list into a ring: no head left
+    out = oracle.list_rank(rec)  # no head: nothing is ranked, and no walk runs away
+    assert out.shape == (10, 2)

@@ -197,6 +197,62 @@ def test_planted_list_mistake_is_caught(name, tmp_path):
     assert not _list_pins_pass(L), f"pins did not catch mutation {name}"
 
 
+# ------------------------------------------------------------------ list ranking
+RANK_MUTATIONS = {
+    "rank_counts_from_one": ("out[2 * v] = len;                     /* nodes before v */",
+                             "out[2 * v] = len + 1;                 /* nodes before v */"),
+    "tail_rank_off_by_one": ("out[2 * v + 1] = len - 1 - out[2 * v];", "out[2 * v + 1] = len - out[2 * v];"),
+    "walks_backwards": ("for (uint64_t v = h; v != ORACLE_NIL; v = rec[2 * v + 1]) {\n            if (len >= n)",
+                        "for (uint64_t v = h; v != ORACLE_NIL; v = rec[2 * v]) {\n            if (len >= n)"),
+    "starts_at_tails": ("if (rec[2 * h] != ORACLE_NIL) continue;   /* not a head */",
+                        "if (rec[2 * h + 1] != ORACLE_NIL) continue;   /* not a head */"),
+}
+
+
+def _compile_rank(src_text, path):
+    L = _compile_list(src_text, path)
+    L.oracle_list_rank.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+    L.oracle_list_rank.restype = ctypes.c_int
+    return L
+
+
+def _rank_pins_pass(L):
+    """Every order of one list for n <= 5 and of two lists for n <= 6: the rank
+    of the k-th visited node of a list of length m is (k, m - 1 - k)."""
+    for n in range(1, 7):
+        for order in itertools.permutations(range(n)):
+            for cut in ([n] if n <= 5 else []) + ([n // 2] if n >= 2 else []):
+                rec = np.full((n, 2), LIST_NIL, dtype=np.uint64)
+                for seg in (order[:cut], order[cut:]):
+                    for k in range(1, len(seg)):
+                        rec[seg[k], 0] = seg[k - 1]
+                        rec[seg[k - 1], 1] = seg[k]
+                out = np.zeros((n, 2), dtype=np.uint64)
+                if L.oracle_list_rank(rec.ctypes.data, n, out.ctypes.data) != 0:
+                    return False
+                for seg in (order[:cut], order[cut:]):
+                    for k, v in enumerate(seg):
+                        if int(out[v, 0]) != k or int(out[v, 1]) != len(seg) - 1 - k:
+                            return False
+    return True
+
+
+def test_real_rank_oracle_passes_compact_pins(tmp_path):
+    with open(LIST_SRC) as f:
+        L = _compile_rank(f.read(), str(tmp_path / "real_rank.so"))
+    assert _rank_pins_pass(L)
+
+
+@pytest.mark.parametrize("name", sorted(RANK_MUTATIONS))
+def test_planted_rank_mistake_is_caught(name, tmp_path):
+    old, new = RANK_MUTATIONS[name]
+    with open(LIST_SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    L = _compile_rank(text.replace(old, new), str(tmp_path / f"{name}.so"))
+    assert not _rank_pins_pass(L), f"pins did not catch mutation {name}"
+
+
 # ---------------------------------------------------------------- tree contraction
 TREE_SRC = os.path.join(ROOT, "oracle", "treec.c")
 
