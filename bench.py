@@ -31,6 +31,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Work queues from the host to the GPU, read when CUDA starts: the serving
+# workload runs a stream per lane next to the tick stream, and streams beyond
+# the queues (8 by default) would wait behind each other's launches.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 PAPER_RP_FINAL_1E9_MS = 3960.0  # RP-Final, n = 1000M 64-bit ints, 72 cores + HT (Table "rp-runtime")
 BYTES_PER_ELEM = {"u32": 72, "u64": 80, "rec128": 96}  # i side r+w + one 32-B sector read + write
@@ -611,6 +615,28 @@ def run_list(args):
     idx = torch.arange(0, n, max(1, n // 100000))
     ok_larger = bool(torch.all((out == -1) | (out > idx[:, None])))
     ms = sorted(times)[len(times) // 2]
+    # list ranking (contraction with link weights, then the reconstruction
+    # step) on the same list: the k-th node of the visiting order has k nodes
+    # before it, checked on a sample
+    rank_times = []
+    for k in range(args.warmup + args.steps):
+        nodes.copy_(base)
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(stream)
+        pip.list_rank(nodes, eps=eps, **opts)
+        e_.record(stream)
+        e_.synchronize()
+        if k >= args.warmup:
+            rank_times.append(s_.elapsed_time(e_))
+    pip.check()
+    ks = torch.arange(0, n, max(1, n // 100000), device="cuda")
+    got = nodes[order[ks]]
+    rank_ok = bool(torch.equal(got[:, 0], ks) and torch.equal(got[:, 1], n - 1 - ks))
+    rms = sorted(rank_times)[len(rank_times) // 2]
+    ranking = {"ms": rms, "value": n / (rms / 1e3), "unit": "ranked nodes/s", "step_ms": rank_times,
+               "sample_check": rank_ok,
+               "what": "pip_list_rank: weighted contraction, then the reconstruction rounds from the largest index "
+                       "down; record i ends as (nodes before i, nodes after i)"}
     ach = LIST_BYTES_PER_NODE * n / (ms / 1e3) / 1e9
     peak, peak_kind = measured_peak_hbm()
     line = {
@@ -625,6 +651,7 @@ def run_list(args):
                                       "smem_bytes", "aux_bound_bytes", "min_rounds")},
         "rounds": st.rounds, "carried_fraction": st.losers / max(1, st.attempts),
         "sample_check": ok_larger,
+        "list_ranking": ranking,
         "paper_context": {"pip_72cores_ht_200M_ms": PAPER_LIST_PIP_200M_MS},
         "gpu_launches": args.steps, "clocks": clk.summary(), "step_ms": times,
     }
@@ -920,7 +947,7 @@ def serve_case(torch, pip, N, opts, plain_N, plain_open=False):
               "throughput_req_s": N / served_span, "elems_s": total / served_span,
               "saturation_req_s": N / t_sat, "saturation_elems_s": total / t_sat,
               "arrival_rate_per_s": rate, "peak_used_bytes": info.peak_used_bytes, "ticks": info.ticks,
-              "big_lane_requests": getattr(info, "big_admitted", None), "clocks": clk.summary()}
+              "lane_requests": info.lane_requests, "clocks": clk.summary()}
     out = {"workload": f"serve_{N}_of_20000_requests_log_uniform_2^12_2^28_u32_u64_eps0.5_budget120GB",
            "served": served, "plain_fifo": plain, "options": dict(opts)}
     if plain.get("saturation_elems_s"):
@@ -1130,19 +1157,37 @@ def main():
             d2h()
 
         h2d_ms, d2h_ms, both_ms = stage(h2d), stage(d2h), stage(both)
+        # one shuffle (of the third buffer, a valid array) while both copies run
+        s3 = torch.cuda.Stream()
+        d2 = buf[2 * slot:2 * slot + nbytes].view(torch.int64 if dtype != "u32" else torch.int32)
+        if dtype == "rec128":
+            d2 = d2.view(-1, 2)
+        torch.cuda.synchronize()
+        a3, b3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s1):
+            d0.copy_(hv, non_blocking=True)
+        with torch.cuda.stream(s2):
+            ov.copy_(d1, non_blocking=True)
+        a3.record(s3)
+        pip.shuffle(d2, seed=seed, eps=eps, stream=s3, **opts)
+        b3.record(s3)
+        torch.cuda.synchronize()
+        pip.check(s3)
+        under_ms = a3.elapsed_time(b3)
         k = args.e2e_steps
-        model = (h2d_ms + d2h_ms + k * max(ms_per_step, both_ms)) / k
+        model = (h2d_ms + d2h_ms + k * max(under_ms, both_ms)) / k
         e2e = {"value": replica_throughput(n, world, k, e2e_ms), "unit": "elems/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "ms_per_step": e2e_ms / k, "steps": k,
                "api": "pip_shuffle_host_stream (pinned host buffers, copies overlapped with neighbouring shuffles)",
                "stages": {"h2d_ms": h2d_ms, "d2h_ms": d2h_ms, "h2d_and_d2h_together_ms": both_ms,
-                          "shuffle_ms": ms_per_step, "h2d_GB_s": nbytes / h2d_ms / 1e6,
+                          "shuffle_ms": ms_per_step, "shuffle_while_copying_ms": under_ms,
+                          "h2d_GB_s": nbytes / h2d_ms / 1e6,
                           "d2h_GB_s": nbytes / d2h_ms / 1e6,
                           "model_ms_per_step": model,
-                          "model": "(h2d + d2h + steps * max(shuffle, h2d and d2h together)) / steps: "
-                                   "the first copy in and the last copy out are not overlapped"}}
-        del host, out, buf, hv, ov, d0, d1
+                          "model": "(h2d + d2h + steps * max(shuffle while copying, h2d and d2h together)) / "
+                                   "steps: the first copy in and the last copy out are not overlapped"}}
+        del host, out, buf, hv, ov, d0, d1, d2
 
     # eps sweep (one timed step each, one warm-up) and its scratch accounting
     sweep = {}

@@ -142,6 +142,12 @@ typedef struct {
  * checked, as the contraction reads it (an error then leaves the records
  * unspecified); the full check costs two random reads per node. */
 #define PIP_FLAG_VALIDATE_INPUT 1024u
+/* Grid driver: launch with an L2 access-policy window that marks the
+ * reservation tables persisting, so that the array's random traffic does not
+ * evict them.  Sets the context's persisting-L2 limit (cudaLimitPersistingL2CacheSize)
+ * to the tables' size, capped by the device's maximum, and leaves it set.
+ * Performance only; results are identical. */
+#define PIP_FLAG_L2_PERSIST_TABLES 2048u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {
@@ -273,8 +279,16 @@ typedef struct {
     uint32_t slot_factor;      /* reservation slots per fresh swap (default 4) */
     uint32_t block_threads;    /* threads per block of the tick kernel (default 512) */
     uint32_t tick_us;          /* GPU time budget of one tick, shared by the resident requests (default 1000) */
-    double prefix_c;           /* C in F = C * n^(1-eps) (default 1) */
+    double prefix_c;           /* C in F = C * n^(1-eps) of tick requests (default 1) */
+    uint32_t lanes;            /* large requests running at once on lanes, each on a stream of its own
+                                  (default: CUDA_DEVICE_MAX_CONNECTIONS - 3, at most 16, i.e. 5 unless that
+                                  variable raises the device's work queues above 8; PIP_SERVE_NO_LANES: none) */
+    uint32_t lane_min_log2;    /* requests of at least 2^lane_min_log2 elements take a lane (default 22) */
+    uint32_t lane_blocks;      /* cap on the grid blocks all lanes hold together (default: half of what the
+                                  persistent grid can keep resident) */
+    uint32_t pad;
 } pip_serve_options;
+#define PIP_SERVE_NO_LANES 0xFFFFFFFFu
 
 /* Per-request record.  Times are host steady-clock nanoseconds. */
 typedef struct {
@@ -289,6 +303,9 @@ typedef struct {
     int64_t done_ns;
     uint32_t ticks;            /* ticks the request was resident for */
     uint32_t fresh_per_round;
+    uint32_t lane_launches;    /* 0: served by tick blocks; else launches on a lane (more than one when
+                                  its blocks did not all meet at the start gate in time) */
+    uint32_t pad;
 } pip_req_stats;
 
 /* Server-wide counters. */
@@ -305,7 +322,11 @@ typedef struct {
     uint32_t tick_blocks;
     uint32_t fresh_cap;
     uint32_t status;           /* PIP_ECUDA once a tick failed */
-    uint32_t pad;
+    uint32_t lane_requests;    /* requests served on a lane so far */
+    uint64_t tick_kernels;     /* tick launches (loop passes with resident tick requests) */
+    uint64_t tick_wait_ns;     /* host time the loop spent waiting for tick launches to finish */
+    uint64_t lane_launches;    /* lane launches, including relaunches after a start gate timed out */
+    uint64_t lane_setup_ns;    /* host time the loop spent queueing lane launches */
 } pip_serve_info;
 
 /*
@@ -317,8 +338,16 @@ typedef struct {
  * time budget in one launch (each request on one block, round state kept in
  * device memory between ticks), and retires finished ones.  Requests arriving meanwhile join at the next
  * tick, so their work overlaps on the device with the requests already
- * running (continuous batching).  The result of every request equals
- * pip_shuffle on the same array, seed and eps.
+ * running (continuous batching).
+ * Large requests (at least 2^lane_min_log2 elements, when their prefix is
+ * large enough for several blocks) take a lane instead: the persistent grid
+ * driver on a slice of the GPU -- about one block per thousand fresh swaps,
+ * within the lanes' block budget -- launched on a low-priority stream next
+ * to the ticks, so that such a request finishes in about the time the whole
+ * grid would take instead of one block's.  A large request waiting for a
+ * lane does not hold back smaller requests behind it.
+ * The result of every request equals pip_shuffle on the same array, seed
+ * and eps.
  */
 pip_status pip_serve_create(pip_server **out, uint64_t device_budget_bytes, int device,
                             const pip_serve_options *opt);
@@ -502,6 +531,39 @@ pip_status pip_list_contract(pip_list_node *nodes_dev, uint64_t n, double eps, v
  * carried to a next round). */
 pip_status pip_list_contract_ex(pip_list_node *nodes_dev, uint64_t n, double eps, const pip_options *opt,
                                 void *aux_dev, uint64_t aux_bytes, pip_stats *stats_dev, void *stream);
+
+/*
+ * pip_list_rank -- list ranking (Section 4.2): list contraction followed by
+ * the reconstruction step, which distributes the values back down the tree
+ * the contraction leaves, both on the relaxed-PIP round engine (about
+ * C * n^(1-eps) nodes a round, the scratch of pip_list_plan).
+ *   nodes_dev: as for pip_list_contract -- n records (prev, next), 16-byte
+ *              aligned, any number of acyclic doubly-linked lists over
+ *              0..n-1 -- overwritten with the result.
+ *   n        : node count, n < 2^31 (distances travel in 32 bits).
+ * On return (stream-ordered) record i holds (nodes before i in its list,
+ * nodes after i in its list), two uint64; a list's length is their sum plus
+ * one.  The contraction keeps, in each node's two words, its nearest larger
+ * node on each side and the distance to it (the node index in the low 32
+ * bits, the distance in the high 32 bits, while it runs); the reconstruction
+ * then takes the nodes from the largest index down: nodes before i = nodes
+ * before its nearest larger node on the left + the distance between them
+ * (the distance minus one when there is none), and likewise after i.  The
+ * result is unique, so it is bit-exact whatever the schedule.
+ * Errors (pip_check): a pointer out of range gives PIP_EINVAL before any
+ * access outside the array, a cycle PIP_EINTERNAL; the records are then
+ * unspecified.  PIP_FLAG_VALIDATE_INPUT in pip_list_rank_ex checks the whole
+ * input first and rejects it untouched (PIP_EINVAL).
+ * Scratch is allocated with cudaMallocAsync on `stream` and freed the same way.
+ */
+pip_status pip_list_rank(pip_list_node *nodes_dev, uint64_t n, double eps, void *stream);
+
+/* pip_list_rank_ex -- the same with the overrides, caller scratch (at least
+ * pip_list_plan's aux_bytes, 256-byte aligned, or NULL) and device stats of
+ * pip_list_contract_ex (rounds, attempts and losers are the contraction's;
+ * status is the whole call's). */
+pip_status pip_list_rank_ex(pip_list_node *nodes_dev, uint64_t n, double eps, const pip_options *opt,
+                            void *aux_dev, uint64_t aux_bytes, pip_stats *stats_dev, void *stream);
 
 /* pip_list_plan -- the plan pip_list_contract_ex would use (host only):
  * elem_bytes = 16, fresh_per_round, max_active, grid_blocks, block_threads,

@@ -137,6 +137,10 @@ class ServeOptions(ctypes.Structure):
         ("block_threads", ctypes.c_uint32),
         ("tick_us", ctypes.c_uint32),
         ("prefix_c", ctypes.c_double),
+        ("lanes", ctypes.c_uint32),
+        ("lane_min_log2", ctypes.c_uint32),
+        ("lane_blocks", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
     ]
 
 
@@ -153,6 +157,8 @@ class ReqStats(ctypes.Structure):
         ("done_ns", ctypes.c_int64),
         ("ticks", ctypes.c_uint32),
         ("fresh_per_round", ctypes.c_uint32),
+        ("lane_launches", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
     ]
 
 
@@ -170,13 +176,18 @@ class ServeInfo(ctypes.Structure):
         ("tick_blocks", ctypes.c_uint32),
         ("fresh_cap", ctypes.c_uint32),
         ("status", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("lane_requests", ctypes.c_uint32),
+        ("tick_kernels", ctypes.c_uint64),
+        ("tick_wait_ns", ctypes.c_uint64),
+        ("lane_launches", ctypes.c_uint64),
+        ("lane_setup_ns", ctypes.c_uint64),
     ]
 
 
 STATS_BYTES = ctypes.sizeof(Stats)
 JOB_STATS_BYTES = ctypes.sizeof(JobStats)
 DRIVER_GRID, DRIVER_CTA, DRIVER_CLUSTER = 0, 1, 2
+SERVE_NO_LANES = 0xFFFFFFFF
 FLAG_SWAP_LOADSTORE = 4
 FLAG_SWAP_EXCHANGE = 8
 FLAG_STORE_EVICT_NORMAL = 16
@@ -186,6 +197,7 @@ FLAG_FORCE_CLUSTER = 128
 FLAG_SPECULATE = 256
 FLAG_TWO_RES = 512
 FLAG_VALIDATE_INPUT = 1024
+FLAG_L2_PERSIST_TABLES = 2048
 
 _lock = threading.Lock()
 _lib = None
@@ -258,6 +270,10 @@ def lib() -> ctypes.CDLL:
         L.pip_list_contract.restype = i32
         L.pip_list_contract_ex.argtypes = [vp, u64, dbl, ctypes.POINTER(Options), vp, u64, vp, vp]
         L.pip_list_contract_ex.restype = i32
+        L.pip_list_rank_ex.argtypes = [vp, u64, dbl, ctypes.POINTER(Options), vp, u64, vp, vp]
+        L.pip_list_rank_ex.restype = i32
+        L.pip_list_rank.argtypes = [vp, u64, dbl, vp]
+        L.pip_list_rank.restype = i32
         L.pip_list_plan.argtypes = [u64, dbl, ctypes.POINTER(Options), ctypes.POINTER(PlanInfo)]
         L.pip_list_plan.restype = i32
         L.pip_tree_contract.argtypes = [vp, u64, dbl, vp]
@@ -630,6 +646,25 @@ def list_contract(nodes, eps: float = 0.5, *, stream=None, aux=None, stats=None,
     rc = lib().pip_list_contract_ex(nodes.data_ptr(), nodes.shape[0], eps, _opt_ptr(make_options(**options)),
                                     aux_ptr, aux_n, st_ptr, _stream_handle(stream))
     _raise(rc, "pip_list_contract_ex")
+
+
+def list_rank(nodes, eps: float = 0.5, *, stream=None, aux=None, stats=None, **options) -> None:
+    """List ranking of the doubly-linked lists in ``nodes`` (``pip_list_rank_ex``;
+    asynchronous on ``stream``): ``nodes`` as for :func:`list_contract`, fewer
+    than 2^31 rows; on return row i holds (nodes before i, nodes after i) in
+    its list.  ``aux``, ``stats`` and the keyword options as in :func:`shuffle`."""
+    if not nodes.is_cuda or not nodes.is_contiguous() or nodes.dim() != 2 or nodes.shape[1] != 2 \
+            or nodes.element_size() != 8:
+        raise ValueError("nodes must be a contiguous (n, 2) CUDA tensor of 8-byte elements")
+    aux_ptr, aux_n = (aux.data_ptr(), aux.numel() * aux.element_size()) if aux is not None else (None, 0)
+    st_ptr = None
+    if stats is not None:
+        if stats.numel() * stats.element_size() < STATS_BYTES:
+            raise ValueError("stats buffer too small")
+        st_ptr = stats.data_ptr()
+    rc = lib().pip_list_rank_ex(nodes.data_ptr(), nodes.shape[0], eps, _opt_ptr(make_options(**options)),
+                                aux_ptr, aux_n, st_ptr, _stream_handle(stream))
+    _raise(rc, "pip_list_rank_ex")
 
 
 # ------------------------------------------------------------------ tree contraction

@@ -83,6 +83,7 @@ namespace {
 #define PIP_MAX_THREADS 512
 #endif
 constexpr int kU = PIP_KU;            // positions per thread in flight in the commit phase
+constexpr uint32_t kGateGo = 1u, kGateAbort = 2u;  // start-gate decisions (Ctrl::gate_decision)
 constexpr unsigned kFull = 0xffffffffu;
 
 
@@ -136,6 +137,30 @@ __device__ __forceinline__ void reserve_fresh(const GridArgs& a, uint32_t lo, ui
   }
 }
 
+// Start gate of a launch that is not cooperative (thread 0 of each block):
+// nothing guarantees that every block is resident at once, so all of them
+// first check in.  The first block that sees every arrival, or runs out of
+// time, decides for all (compare-and-swap on one word); on an abort every
+// block leaves before touching the array or the tables, and the run reports
+// PIP_EBUSY.  Returns true when the blocks may go on.
+__device__ __noinline__ bool start_gate(Ctrl* ctrl, uint64_t timeout_ns) {
+  atomicAdd(&ctrl->gate_count, 1u);
+  uint64_t t0 = 0;
+  uint32_t polls = 0, d;
+  while ((d = ld_relaxed_u32(&ctrl->gate_decision)) == 0u) {
+    if (ld_relaxed_u32(&ctrl->gate_count) >= gridDim.x) {
+      atomicCAS(&ctrl->gate_decision, 0u, kGateGo);
+    } else if ((++polls & 63u) == 0u) {
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > timeout_ns) atomicCAS(&ctrl->gate_decision, 0u, kGateAbort);
+    }
+  }
+  fence_acq_rel_gpu();
+  if (d == kGateAbort) set_status(&ctrl->status, PIP_EBUSY);
+  return d == kGateGo;
+}
+
 __device__ __forceinline__ void clear_words(uint32_t* p, uint32_t count, uint32_t tid, uint32_t T) {
   // 16-byte stores over the 16-byte aligned body, scalars for the tail
   const uint32_t n4 = count >> 2;
@@ -147,7 +172,7 @@ __device__ __forceinline__ void clear_words(uint32_t* p, uint32_t count, uint32_
 // Words of a window bitmap over F locations.
 __host__ __device__ __forceinline__ uint32_t window_words(uint32_t F) { return (F + 31u) >> 5; }
 
-template <typename Elem, bool kExplicit>
+template <typename Elem, bool kExplicit, bool kGate>
 __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel(const GridArgs a) {
   // two on-chip loser lists of a.kloc words: the block's losers of the
   // previous round (worked on now) and of this round (worked on next)
@@ -194,6 +219,11 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
   }
   __syncthreads();
   if (s_start_status != 0u) goto done;
+  if constexpr (kGate) {
+    if (threadIdx.x == 0) s_stop = start_gate(ctrl, a.gate_timeout_ns) ? 0u : 2u;
+    __syncthreads();
+    if (s_stop != 0u) goto done;
+  }
 
   // ---- prologue: W_0 reserves for round 0 (barrier 0 uses word bw[0];
   // round r's barrier uses bw[(r+1)%3])
@@ -437,9 +467,9 @@ __global__ void validate_targets_kernel(const uint32_t* __restrict__ H, uint32_t
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(&ctrl->status, PIP_EINVAL);
 }
 
-template <typename Elem, bool kExplicit>
+template <typename Elem, bool kExplicit, bool kGate = false>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&rounds_kernel<Elem, kExplicit>);
+  return reinterpret_cast<const void*>(&rounds_kernel<Elem, kExplicit, kGate>);
 }
 
 const void* select_kernel(uint32_t elem_bytes, bool explicit_h) {
@@ -447,6 +477,16 @@ const void* select_kernel(uint32_t elem_bytes, bool explicit_h) {
     case 4: return explicit_h ? kernel_ptr<uint32_t, true>() : kernel_ptr<uint32_t, false>();
     case 8: return explicit_h ? kernel_ptr<unsigned long long, true>() : kernel_ptr<unsigned long long, false>();
     case 16: return explicit_h ? kernel_ptr<uint4, true>() : kernel_ptr<uint4, false>();
+    default: return nullptr;
+  }
+}
+
+// The gated kernels (hashed targets only): serving lanes.
+const void* select_gated_kernel(uint32_t elem_bytes) {
+  switch (elem_bytes) {
+    case 4: return kernel_ptr<uint32_t, false, true>();
+    case 8: return kernel_ptr<unsigned long long, false, true>();
+    case 16: return kernel_ptr<uint4, false, true>();
     default: return nullptr;
   }
 }
@@ -509,9 +549,13 @@ uint32_t grid_driver_max_blocks(uint32_t elem_bytes, bool explicit_h, uint32_t t
   return (uint32_t)it->second * (uint32_t)di.sms;
 }
 
-pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
-                              pip_stats* stats, cudaStream_t stream) {
-  const void* k = select_kernel(plan.elem_bytes, H != nullptr);
+namespace {
+
+pip_status launch_grid_common(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
+                              pip_stats* stats, uint64_t gate_timeout_ns, cudaStream_t stream) {
+  const bool gated = gate_timeout_ns != 0u;
+  if (gated && H != nullptr) return PIP_EINVAL;
+  const void* k = gated ? select_gated_kernel(plan.elem_bytes) : select_kernel(plan.elem_bytes, H != nullptr);
   if (k == nullptr) return PIP_EINVAL;
   char* base = static_cast<char*>(aux);
   GridArgs a{};
@@ -534,7 +578,9 @@ pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint
   a.max_rounds = plan.n + 8u;
   a.deadline_ns = plan.deadline_ns;
   a.flags = plan.flags;
-  a.latch = error_latch_ptr();
+  a.gate_timeout_ns = gate_timeout_ns;
+  // a lane keeps its errors to itself: they are the request's, not the device's
+  a.latch = gate_timeout_ns != 0u ? &a.ctrl->lane_status : error_latch_ptr();
   if (a.latch == nullptr) return PIP_ECUDA;
 
   if (cudaMemsetAsync(aux, 0, plan.aux_bytes, stream) != cudaSuccess) return PIP_ECUDA;
@@ -543,7 +589,8 @@ pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint
     validate_targets_kernel<<<vb, 256, 0, stream>>>(H, plan.n, a.ctrl);
     if (cudaGetLastError() != cudaSuccess) return PIP_ECUDA;
   }
-  // every block must be co-resident (the cooperative launch refuses otherwise)
+  // every block must be co-resident (the cooperative launch refuses otherwise;
+  // a gated launch checks it at its start gate)
   uint32_t blocks = plan.blocks;
   const uint32_t maxb = grid_driver_max_blocks(plan.elem_bytes, H != nullptr, plan.threads, plan.kloc);
   if (maxb == 0) return PIP_ECUDA;
@@ -553,17 +600,56 @@ pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint
   cfg.blockDim = dim3(plan.threads);
   cfg.dynamicSmemBytes = grid_block_smem(plan.kloc);
   cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (!gated) {
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+  }
+  if (plan.flags & PIP_FLAG_L2_PERSIST_TABLES) {
+    // the three slot tables are contiguous in the scratch layout
+    const uint64_t lo = plan.off_S[0], hi = plan.off_S[2] + 4ull * plan.nslots;
+    int dev = 0, max_persist = 0, max_window = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev) == cudaSuccess &&
+        max_persist > 0 && max_window > 0) {
+      const size_t want = (size_t)std::min<uint64_t>(hi - lo, (uint64_t)max_persist);
+      size_t cur = 0;
+      if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess && cur < want)
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+      attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+      attr[na].val.accessPolicyWindow.base_ptr = base + lo;
+      attr[na].val.accessPolicyWindow.num_bytes = (size_t)std::min<uint64_t>(hi - lo, (uint64_t)max_window);
+      attr[na].val.accessPolicyWindow.hitRatio = 1.0f;
+      attr[na].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+      attr[na].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+      ++na;
+    }
+    cudaGetLastError();
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = na;
   void* args[] = {&a};
   if (cudaLaunchKernelExC(&cfg, k, args) != cudaSuccess) {
     cudaGetLastError();
     return PIP_ECUDA;
   }
   return PIP_OK;
+}
+
+}  // namespace
+
+pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint64_t seed, void* aux,
+                              pip_stats* stats, cudaStream_t stream) {
+  return launch_grid_common(plan, A, H, seed, aux, stats, 0, stream);
+}
+
+pip_status launch_grid_lane(const Plan& plan, void* A, uint64_t seed, void* aux, pip_stats* stats,
+                            uint64_t gate_timeout_ns, cudaStream_t stream) {
+  if (gate_timeout_ns == 0u) return PIP_EINVAL;
+  return launch_grid_common(plan, A, nullptr, seed, aux, stats, gate_timeout_ns, stream);
 }
 
 }  // namespace pip

@@ -20,7 +20,13 @@ struct Ctrl {
   // and of the losers they could not keep on chip (field layout in
   // device.cuh).
   unsigned long long bw[3];
-  uint32_t pad[52];
+  // Start gate of a grid-driver launch that is not cooperative (a serving
+  // lane): arriving blocks, and the decision (kGateGo / kGateAbort) taken by
+  // the first block that sees all arrivals or runs out of time.
+  uint32_t gate_count;
+  uint32_t gate_decision;
+  uint32_t lane_status;  // error latch of a lane launch (instead of the per-device one)
+  uint32_t pad[49];
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is one 256-byte line pair");
 
@@ -70,6 +76,7 @@ struct GridArgs {
   uint32_t flags;
   uint32_t* latch;     // per-device error latch
   uint64_t deadline_ns;  // whole-kernel time limit
+  uint64_t gate_timeout_ns;  // > 0: blocks meet at a start gate first (non-cooperative launch)
 };
 
 // One array of a block-resident (batched) run.  40 bytes.
@@ -213,6 +220,15 @@ uint32_t elem_bytes_of(pip_dtype dtype);
 // validation (if H is given), then the persistent kernel, on `stream`.
 pip_status launch_grid_driver(const Plan& plan, void* A, const uint32_t* H, uint64_t seed,
                               void* aux, pip_stats* stats, cudaStream_t stream);
+// The same persistent grid driver launched without the cooperative attribute,
+// for a serving lane that runs next to other kernels: `plan.blocks` blocks
+// first meet at a start gate, and if they are not all resident within
+// `gate_timeout_ns` every block leaves before touching the array or the
+// tables, and the run reports PIP_EBUSY (it can simply be launched again).
+// Errors go to the launch's own status word in the Ctrl block (and to
+// `stats`), not to the per-device latch.
+pip_status launch_grid_lane(const Plan& plan, void* A, uint64_t seed, void* aux, pip_stats* stats,
+                            uint64_t gate_timeout_ns, cudaStream_t stream);
 // Device address of the per-device error latch (current device), or nullptr.
 uint32_t* error_latch_ptr();
 // Reads and clears the latch of the current device (synchronous).

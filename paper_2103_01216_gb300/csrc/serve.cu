@@ -15,11 +15,22 @@
 //      their scratch, and wake the clients waiting on them.
 // Requests that arrive while others are on the GPU join at the next tick,
 // and the work of all resident requests overlaps on the device.
+//
+// Large requests take a lane instead of a tick block: one launch of the
+// persistent grid driver with a few dozen blocks (about one per thousand
+// fresh swaps of its prefix) on a low-priority stream of its own, next to
+// the ticks.  One block would need the request's whole length in rounds of
+// a ~1K prefix; the lane's prefix is the one the scratch bound allows, so a
+// 2^28-element request takes tens of milliseconds instead of about a
+// second.  A lane launch is not cooperative (the ticks hold SMs too), so its
+// blocks first meet at a start gate: if they are not all resident in time
+// they leave before touching anything, and the loop launches it again.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -46,27 +57,47 @@ int64_t now_ns() {
       .count();
 }
 
+// Work counter and start time of one tick, cleared before every launch.
+struct TickCtl {
+  uint32_t next;
+  uint32_t pad;
+  unsigned long long start;  // globaltimer of the first block to start
+};
+
+// One tick: blocks take resident requests in the order of `work` and
+// advance each for a time slice.  The tick ends `tick_ns` after its first
+// block started, whatever the residency: a block that starts late (SMs held
+// by lane launches) takes a shorter slice or no request, so one tick never
+// stretches into several while the lanes run.
 __global__ void __launch_bounds__(1024) serve_tick_kernel(ServeSlot* slots, const uint32_t* work, uint32_t count,
-                                                          uint32_t* next, uint32_t fmax, uint32_t sigma,
-                                                          uint32_t budget, uint64_t deadline_ns, uint64_t slice_ns) {
+                                                          TickCtl* ctl, uint32_t fmax, uint32_t sigma,
+                                                          uint32_t budget, uint64_t deadline_ns, uint64_t slice_ns,
+                                                          uint64_t tick_ns) {
   extern __shared__ uint32_t smem[];
   __shared__ uint32_t s_w;
+  __shared__ uint64_t s_slice;
   const uint64_t t0 = globaltimer_ns();
+  if (threadIdx.x == 0) atomicCAS(&ctl->start, 0ull, (unsigned long long)t0);
   for (;;) {
-    if (threadIdx.x == 0) s_w = atomicAdd(next, 1u);
+    if (threadIdx.x == 0) {
+      const uint64_t end = ld_relaxed_u64(&ctl->start) + tick_ns, now = globaltimer_ns();
+      s_w = now + 10000ull < end ? atomicAdd(&ctl->next, 1u) : count;  // less than 10 us left: stop
+      s_slice = now < end ? min(slice_ns, end - now) : 0ull;
+    }
     __syncthreads();
     const uint32_t w = s_w;
+    const uint64_t slice = s_slice;
     __syncthreads();
     if (w >= count) break;
     ServeSlot* sl = slots + work[w];
     const BatchJob job = sl->job;
     uint32_t st;
     if (sl->elem_bytes == 4)
-      st = run_job<uint32_t>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false, slice_ns);
+      st = run_job<uint32_t>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false, slice);
     else if (sl->elem_bytes == 8)
       st = run_job<unsigned long long>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false,
-                                       slice_ns);
-    else st = run_job<uint4>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false, slice_ns);
+                                       slice);
+    else st = run_job<uint4>(job, smem, fmax, sigma, deadline_ns, t0, nullptr, &sl->rs, budget, false, slice);
     (void)st;  // the status is in the request's round state
   }
 }
@@ -94,6 +125,12 @@ struct Req {
   uint64_t array_bytes = 0;
   uint64_t aux_bytes = 0;
   int slot = -1;
+  // lane requests: the grid plan, its scratch, the lane running it
+  bool lane_ok = false;
+  Plan plan;
+  void* aux = nullptr;
+  int lane = -1;
+  uint32_t lane_retries = 0;
   bool done = false;
   bool released = false;
   uint32_t status = 0;
@@ -102,6 +139,21 @@ struct Req {
   uint32_t ticks = 0;
   int64_t submit_ns = 0, admit_ns = 0, done_ns = 0;
 };
+
+// One lane: a low-priority stream, the completion event of its current
+// launch and the launch's statistics (device record and its host copy).
+struct Lane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  pip_stats* d_stats = nullptr;
+  pip_stats* h_stats = nullptr;
+  Req* req = nullptr;
+};
+
+constexpr uint64_t kLaneGateNs = 200000000ull;  // a lane's blocks must all be resident within 200 ms
+constexpr uint32_t kLaneMinF = 2048;             // smaller prefixes stay on one block
+constexpr uint32_t kLaneMaxRetries = 8;
+constexpr uint32_t kMaxAdmitSkips = 512;         // waiting requests one admission pass may step over
 
 }  // namespace
 }  // namespace pip
@@ -121,12 +173,24 @@ struct pip_server {
   pip::ServeSlot* h_slots = nullptr;
   uint32_t* d_work = nullptr;
   uint32_t* h_work = nullptr;
-  uint32_t* d_next = nullptr;
+  pip::TickCtl* d_next = nullptr;
   std::vector<int> free_slots;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<pip::Req*> waiting;
   std::vector<pip::Req*> resident;
+  // lanes
+  std::vector<pip::Lane> lanes;
+  uint32_t lane_min_log2 = 22, lane_block_budget = 0, lane_blocks_used = 0;
+  uint64_t lane_requests = 0, lane_launches = 0, tick_kernels = 0, tick_wait_ns = 0, lane_setup_ns = 0;
+  std::vector<pip::Req*> lane_resident;
+  uint64_t wake = 0;  // bumped by every submission and release (the loop's idle wait watches it)
+  // The server's own memory pool.  The streams of the ticks and of the lanes
+  // share it, and it never makes one stream wait for another to reuse memory
+  // (no internal dependencies): with the default pool, an allocation on the
+  // tick stream could be made to wait for a lane's long kernel.  It keeps
+  // freed memory mapped up to the budget.
+  cudaMemPool_t pool = nullptr;
   std::unordered_map<uint64_t, pip::Req*> reqs;
   std::vector<void*> to_free;  // released server-owned arrays, freed by the loop thread
   std::deque<uint64_t> finished;  // tickets in completion order, not yet handed out by next_done
@@ -146,40 +210,123 @@ uint64_t req_aux_bytes(uint32_t F) { return (uint64_t)cta_kmax(F) * 4 + sizeof(S
 }  // namespace
 }  // namespace pip
 
+namespace pip {
+namespace {
+
+// Queues a lane request's launch on its lane's stream: its array (when the
+// server owns it), its scratch, the gated grid driver, the copy of its
+// statistics and the completion event.  False when an allocation or a
+// launch failed (the request then fails alone).
+bool lane_launch(Lane& L, Req* r, bool first, cudaMemPool_t pool, uint64_t* launches) {
+  if (first && r->A == nullptr && r->n > 0) {
+    r->owned = true;
+    if (cudaMallocFromPoolAsync(&r->A, r->array_bytes, pool, L.stream) != cudaSuccess) {
+      cudaGetLastError();
+      r->A = nullptr;
+      r->status = PIP_ENOMEM;
+      return false;
+    }
+    init_array_kernel<<<std::min<uint64_t>(4096, (r->n + 255) / 256 + 1), 256, 0, L.stream>>>(
+        r->A, (uint32_t)r->n, r->elem_bytes);
+  }
+  if (first) {
+    if (cudaMallocFromPoolAsync(&r->aux, r->plan.aux_bytes, pool, L.stream) != cudaSuccess) {
+      cudaGetLastError();
+      r->aux = nullptr;
+      r->status = PIP_ENOMEM;
+      return false;
+    }
+  }
+  ++*launches;
+  if (launch_grid_lane(r->plan, r->A, r->seed, r->aux, L.d_stats, kLaneGateNs, L.stream) != PIP_OK ||
+      cudaMemcpyAsync(L.h_stats, L.d_stats, sizeof(pip_stats), cudaMemcpyDeviceToHost, L.stream) != cudaSuccess ||
+      cudaEventRecord(L.done, L.stream) != cudaSuccess) {
+    cudaGetLastError();
+    r->status = PIP_ECUDA;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+}  // namespace pip
+
 void pip_server::loop() {
   using namespace pip;
   cudaSetDevice(device);
-  std::vector<Req*> admit_now;
+  std::vector<Req*> admit_now, admit_lane;
+  std::vector<Req*> lane_failed;
+  uint64_t seen_wake = 0;
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stop || !waiting.empty() || !resident.empty() || !to_free.empty(); });
-      if (stop && resident.empty()) break;
+      cv_work.wait(lk, [&] {
+        return stop || !waiting.empty() || !resident.empty() || !lane_resident.empty() || !to_free.empty();
+      });
+      if (stop && resident.empty() && lane_resident.empty()) break;
+      seen_wake = wake;
       for (void* p : to_free) cudaFreeAsync(p, stream);
       to_free.clear();
-      // admission in arrival order (a request that does not fit blocks the ones behind it)
+      // Admission in arrival order: a request that does not fit the budget
+      // blocks the ones behind it; a large request that only waits for a
+      // lane (or a small one that waits for a tick slot) does not.
       admit_now.clear();
-      while (!stop && !waiting.empty() && !free_slots.empty()) {
-        Req* r = waiting.front();
+      admit_lane.clear();
+      int free_lane = -1;
+      for (size_t j = 0; j < lanes.size(); ++j)
+        if (lanes[j].req == nullptr) free_lane = (int)j;
+      uint32_t skipped = 0;  // bounds the scan past requests that wait for a lane or a slot
+      for (auto it = waiting.begin(); !stop && it != waiting.end() && skipped < kMaxAdmitSkips;) {
+        const bool slot_free = !free_slots.empty();
+        if (!slot_free && free_lane < 0) break;
+        Req* r = *it;
         const uint64_t charge = r->array_bytes + r->aux_bytes;
         if (used + charge > budget) break;
-        waiting.pop_front();
+        if (r->lane_ok) {
+          if (free_lane < 0 || lane_blocks_used + r->plan.blocks > lane_block_budget) {
+            ++it;
+            ++skipped;
+            continue;
+          }
+          r->lane = free_lane;
+          lanes[free_lane].req = r;
+          lane_blocks_used += r->plan.blocks;
+          lane_resident.push_back(r);
+          admit_lane.push_back(r);
+          ++lane_requests;
+          free_lane = -1;
+          for (size_t j = 0; j < lanes.size(); ++j)
+            if (lanes[j].req == nullptr) free_lane = (int)j;
+        } else {
+          if (!slot_free) {
+            ++it;
+            ++skipped;
+            continue;
+          }
+          r->slot = free_slots.back();
+          free_slots.pop_back();
+          admit_now.push_back(r);
+          resident.push_back(r);
+        }
+        it = waiting.erase(it);
         used += charge;
         peak_used = std::max(peak_used, used);
-        r->slot = free_slots.back();
-        free_slots.pop_back();
         r->admit_ns = now_ns();
-        admit_now.push_back(r);
-        resident.push_back(r);
         ++admitted;
       }
     }
+    // launch the newly admitted lane requests (stream-ordered on their lanes)
+    lane_failed.clear();
+    const int64_t t_lane = now_ns();
+    for (Req* r : admit_lane)
+      if (!lane_launch(lanes[r->lane], r, true, pool, &lane_launches)) lane_failed.push_back(r);
+    lane_setup_ns += (uint64_t)(now_ns() - t_lane);
     // set up the newly admitted requests (allocations and copies are stream-ordered)
     for (Req* r : admit_now) {
       bool ok = true;
       if (r->A == nullptr && r->n > 0) {
         r->owned = true;
-        if (cudaMallocAsync(&r->A, r->array_bytes, stream) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&r->A, r->array_bytes, pool, stream) != cudaSuccess) {
           cudaGetLastError();
           r->A = nullptr;
           ok = false;
@@ -189,7 +336,7 @@ void pip_server::loop() {
         }
       }
       if (ok && r->n >= 2) {
-        if (cudaMallocAsync(reinterpret_cast<void**>(&r->Q), (uint64_t)cta_kmax(r->F) * 4, stream) !=
+        if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->Q), (uint64_t)cta_kmax(r->F) * 4, pool, stream) !=
             cudaSuccess) {
           cudaGetLastError();
           r->Q = nullptr;
@@ -213,9 +360,10 @@ void pip_server::loop() {
       }
       cudaMemcpyAsync(d_slots + r->slot, &hs, sizeof(ServeSlot), cudaMemcpyHostToDevice, stream);
     }
-    // one tick over every resident request, the most remaining work first
-    // (the largest requests set the makespan), each for a time slice that
-    // spreads the tick's time budget over the requests per block
+    // one tick over the resident requests, the least remaining work first
+    // (the large requests run on lanes; among the rest, finishing the short
+    // ones first keeps their latency at a tick or two), each for a time slice
+    // that spreads the tick's time budget over the requests per block
     uint32_t count = 0;
     int max_slot = -1;
     std::vector<std::pair<uint64_t, int>> order;
@@ -227,19 +375,55 @@ void pip_server::loop() {
       max_slot = std::max(max_slot, r->slot);
       r->ticks += 1;
     }
-    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
     for (const auto& o : order) h_work[count++] = (uint32_t)o.second;
     if (count > 0) {
       cudaMemcpyAsync(d_work, h_work, count * sizeof(uint32_t), cudaMemcpyHostToDevice, stream);
-      cudaMemsetAsync(d_next, 0, sizeof(uint32_t), stream);
+      cudaMemsetAsync(d_next, 0, sizeof(TickCtl), stream);
       const uint32_t grid = std::max(1u, std::min(count, blocks));
       const uint64_t waves = (count + grid - 1) / grid;
       const uint64_t slice = std::max<uint64_t>(20000ull, tick_ns / waves);
       serve_tick_kernel<<<grid, threads, smem, stream>>>(d_slots, d_work, count, d_next, fmax, sigma,
-                                                         rounds_per_tick, 120000000000ull, slice);
+                                                         rounds_per_tick, 120000000000ull, slice, tick_ns);
       cudaMemcpyAsync(h_slots, d_slots, (size_t)(max_slot + 1) * sizeof(ServeSlot), cudaMemcpyDeviceToHost, stream);
     }
+    const int64_t t_sync = now_ns();
     const cudaError_t e = cudaStreamSynchronize(stream);
+    if (count > 0) {
+      ++tick_kernels;
+      tick_wait_ns += (uint64_t)(now_ns() - t_sync);
+    }
+    if (count == 0 && admit_lane.empty() && admit_now.empty()) {
+      // no tick ran: wait for a lane to finish (polled), a submission or a
+      // release, instead of spinning
+      std::unique_lock<std::mutex> lk(mu);
+      const auto limit = lane_resident.empty() ? std::chrono::microseconds(5000) : std::chrono::microseconds(100);
+      cv_work.wait_for(lk, limit, [&] { return stop || wake != seen_wake; });
+    }
+    // lanes whose launch finished: retire the request, or launch it again
+    // when its blocks could not all meet at the start gate
+    std::vector<Req*> lane_done;
+    for (Lane& L : lanes) {
+      Req* r = L.req;
+      if (r == nullptr || std::find(lane_failed.begin(), lane_failed.end(), r) != lane_failed.end()) continue;
+      const cudaError_t q = cudaEventQuery(L.done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        r->status = PIP_ECUDA;
+      } else {
+        r->status = L.h_stats->status;
+        r->rounds = L.h_stats->rounds;
+        r->attempts = L.h_stats->attempts;
+        r->losers = L.h_stats->losers;
+        if (r->status == PIP_EBUSY && r->lane_retries < kLaneMaxRetries) {
+          ++r->lane_retries;
+          if (lane_launch(L, r, false, pool, &lane_launches)) continue;
+        }
+      }
+      lane_done.push_back(r);
+    }
+    for (Req* r : lane_failed) lane_done.push_back(r);
     const int64_t t = now_ns();
     {
       std::lock_guard<std::mutex> lk(mu);
@@ -276,10 +460,31 @@ void pip_server::loop() {
         }
       }
       resident.swap(still);
+      for (Req* r : lane_done) {
+        Lane& L = lanes[r->lane];
+        r->done = true;
+        r->done_ns = t;
+        r->ticks += 1;
+        if (r->aux != nullptr) cudaFreeAsync(r->aux, L.stream);
+        r->aux = nullptr;
+        used -= r->aux_bytes;
+        lane_blocks_used -= r->plan.blocks;
+        L.req = nullptr;
+        ++completed;
+        finished.push_back(r->ticket);
+        if (r->status != PIP_OK && r->owned) {
+          if (r->A != nullptr) cudaFreeAsync(r->A, L.stream);
+          r->A = nullptr;
+          used -= r->array_bytes;
+          r->array_bytes = 0;
+        }
+        lane_resident.erase(std::find(lane_resident.begin(), lane_resident.end(), r));
+      }
     }
     cv_done.notify_all();
   }
   cudaStreamSynchronize(stream);
+  for (Lane& L : lanes) cudaStreamSynchronize(L.stream);
 }
 
 extern "C" {
@@ -333,12 +538,18 @@ pip_status pip_serve_create(pip_server** out, uint64_t device_budget_bytes, int 
   // so every resident request advances for the whole tick (requests beyond
   // that wait in the arrival-ordered admission queue)
   if (s->opt.max_resident == 0) s->max_resident = s->blocks;
-  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+  // the tick stream has the highest priority: as SMs free up, the blocks of
+  // the next tick (the small requests, each a few ticks long) are placed
+  // ahead of pending lane blocks
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  cudaGetLastError();
+  if (cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaMalloc(&s->d_slots, sizeof(ServeSlot) * s->max_resident) != cudaSuccess ||
       cudaMallocHost(&s->h_slots, sizeof(ServeSlot) * s->max_resident) != cudaSuccess ||
       cudaMalloc(&s->d_work, sizeof(uint32_t) * s->max_resident) != cudaSuccess ||
       cudaMallocHost(&s->h_work, sizeof(uint32_t) * s->max_resident) != cudaSuccess ||
-      cudaMalloc(&s->d_next, sizeof(uint32_t)) != cudaSuccess) {
+      cudaMalloc(&s->d_next, sizeof(pip::TickCtl)) != cudaSuccess) {
     cudaGetLastError();
     if (s->stream) cudaStreamDestroy(s->stream);
     cudaFree(s->d_slots);
@@ -350,6 +561,75 @@ pip_status pip_serve_create(pip_server** out, uint64_t device_budget_bytes, int 
     return PIP_ENOMEM;
   }
   for (int j = (int)s->max_resident - 1; j >= 0; --j) s->free_slots.push_back(j);
+  {
+    cudaMemPoolProps pp{};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    int no = 0, yes = 1;
+    uint64_t keep = device_budget_bytes;
+    if (cudaMemPoolCreate(&s->pool, &pp) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowOpportunistic, &yes) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      if (s->pool) cudaMemPoolDestroy(s->pool);
+      cudaStreamDestroy(s->stream);
+      cudaFree(s->d_slots);
+      cudaFreeHost(s->h_slots);
+      cudaFree(s->d_work);
+      cudaFreeHost(s->h_work);
+      cudaFree(s->d_next);
+      delete s;
+      return PIP_ECUDA;
+    }
+  }
+  // lanes: streams of the lowest priority (their persistent launches take
+  // what the ticks leave)
+  // Each stream needs a host-to-device work queue of its own: streams that
+  // share one (CUDA_DEVICE_MAX_CONNECTIONS, default 8) queue behind each
+  // other's launches, and a tick would then wait for a lane's persistent
+  // launch.  The default keeps the tick stream and the lanes within the
+  // connections, with two to spare for the caller's streams.
+  uint32_t connections = 8;
+  if (const char* e = std::getenv("CUDA_DEVICE_MAX_CONNECTIONS")) {
+    const long v = std::atol(e);
+    if (v >= 1 && v <= 32) connections = (uint32_t)v;
+  }
+  const uint32_t lanes_default = connections > 3 ? std::min(16u, connections - 3) : 0u;
+  const uint32_t nl = s->opt.lanes == PIP_SERVE_NO_LANES ? 0u : (s->opt.lanes ? s->opt.lanes : lanes_default);
+  s->lane_min_log2 = s->opt.lane_min_log2 ? s->opt.lane_min_log2 : 22u;
+  const uint32_t grid_cap = grid_driver_max_blocks(8, false, 512, 1024);
+  s->lane_block_budget = s->opt.lane_blocks ? std::min(s->opt.lane_blocks, grid_cap) : grid_cap / 2;
+  bool lanes_ok = true;
+  for (uint32_t j = 0; j < nl && lanes_ok; ++j) {
+    Lane L;
+    lanes_ok = cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, prio_lo) == cudaSuccess &&
+               cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) == cudaSuccess &&
+               cudaMalloc(&L.d_stats, sizeof(pip_stats)) == cudaSuccess &&
+               cudaMallocHost(&L.h_stats, sizeof(pip_stats)) == cudaSuccess;
+    s->lanes.push_back(L);
+  }
+  if (!lanes_ok) {
+    cudaGetLastError();
+    for (Lane& L : s->lanes) {
+      if (L.stream) cudaStreamDestroy(L.stream);
+      if (L.done) cudaEventDestroy(L.done);
+      cudaFree(L.d_stats);
+      cudaFreeHost(L.h_stats);
+    }
+    s->lanes.clear();
+    cudaMemPoolDestroy(s->pool);
+    cudaStreamDestroy(s->stream);
+    cudaFree(s->d_slots);
+    cudaFreeHost(s->h_slots);
+    cudaFree(s->d_work);
+    cudaFreeHost(s->h_work);
+    cudaFree(s->d_next);
+    delete s;
+    return PIP_ENOMEM;
+  }
   s->th = std::thread([s] { s->loop(); });
   *out = s;
   return PIP_OK;
@@ -374,6 +654,31 @@ pip_status pip_serve_submit(pip_server* s, void* A_dev, uint64_t n, pip_dtype dt
   r->F = n >= 2 ? cta_fresh(n, eps, &o, s->sigma, s->fmax) : 1u;
   r->array_bytes = n * eb;
   r->aux_bytes = req_aux_bytes(r->F);
+  if (!s->lanes.empty() && s->lane_min_log2 < 64 && n >= (1ull << s->lane_min_log2)) {
+    // a lane: the grid plan the scratch bound allows, on about one block of
+    // 512 threads per thousand fresh swaps (two positions per thread)
+    int cur = -1;
+    const bool switch_dev = cudaGetDevice(&cur) == cudaSuccess && cur != s->device;
+    if (switch_dev) cudaSetDevice(s->device);
+    pip_options g{};
+    g.flags = PIP_FLAG_FORCE_GRID;
+    g.block_threads = 512;
+    g.slot_factor = s->sigma;
+    Plan p0;
+    if (make_plan(n, dtype, eps, &g, &p0) == PIP_OK && p0.F >= kLaneMinF) {
+      const uint64_t want = (5ull * p0.F / 4 + 1023) / 1024;
+      g.grid_blocks = (uint32_t)std::min<uint64_t>(64, std::max<uint64_t>(2, want));
+      Plan p1;
+      if (make_plan(n, dtype, eps, &g, &p1) == PIP_OK && p1.blocks <= s->lane_block_budget) {
+        r->lane_ok = true;
+        r->plan = p1;
+        r->F = p1.F;
+        r->aux_bytes = p1.aux_bytes;
+      }
+    }
+    cudaGetLastError();
+    if (switch_dev) cudaSetDevice(cur);
+  }
   if (r->array_bytes + r->aux_bytes > s->budget) {
     delete r;
     return PIP_EINVAL;  // can never be admitted
@@ -385,6 +690,7 @@ pip_status pip_serve_submit(pip_server* s, void* A_dev, uint64_t n, pip_dtype dt
     s->reqs[r->ticket] = r;
     s->waiting.push_back(r);
     ++s->submitted;
+    ++s->wake;
     *ticket = r->ticket;
   }
   s->cv_work.notify_one();
@@ -405,6 +711,7 @@ static void fill_stats(const pip::Req* r, pip_req_stats* st) {
   st->done_ns = r->done_ns;
   st->ticks = r->ticks;
   st->fresh_per_round = r->F;
+  st->lane_launches = r->lane >= 0 ? r->lane_retries + 1u : 0u;
 }
 
 pip_status pip_serve_poll(pip_server* s, uint64_t ticket, void** A_out, pip_req_stats* st) {
@@ -457,6 +764,7 @@ pip_status pip_serve_release(pip_server* s, uint64_t ticket) {
     if (r->owned && r->A != nullptr) s->to_free.push_back(r->A);
     s->used -= r->array_bytes;
     s->reqs.erase(it);
+    ++s->wake;
     delete r;
   }
   s->cv_work.notify_one();
@@ -479,6 +787,11 @@ pip_status pip_serve_info_get(pip_server* s, pip_serve_info* out) {
   out->tick_blocks = s->blocks;
   out->fresh_cap = s->fmax;
   out->status = s->loop_error;
+  out->lane_requests = (uint32_t)s->lane_requests;
+  out->tick_kernels = s->tick_kernels;
+  out->tick_wait_ns = s->tick_wait_ns;
+  out->lane_launches = s->lane_launches;
+  out->lane_setup_ns = s->lane_setup_ns;
   return PIP_OK;
 }
 
@@ -497,14 +810,23 @@ pip_status pip_serve_destroy(pip_server* s) {
   s->cv_work.notify_all();
   if (s->th.joinable()) s->th.join();
   cudaSetDevice(s->device);
+  for (pip::Lane& L : s->lanes) cudaStreamSynchronize(L.stream);
   for (auto& kv : s->reqs) {
     pip::Req* r = kv.second;
     if (r->owned && r->A != nullptr) cudaFreeAsync(r->A, s->stream);
     if (r->Q != nullptr) cudaFreeAsync(r->Q, s->stream);
+    if (r->aux != nullptr) cudaFreeAsync(r->aux, s->stream);
     delete r;
+  }
+  for (pip::Lane& L : s->lanes) {
+    cudaStreamDestroy(L.stream);
+    cudaEventDestroy(L.done);
+    cudaFree(L.d_stats);
+    cudaFreeHost(L.h_stats);
   }
   for (void* p : s->to_free) cudaFreeAsync(p, s->stream);
   cudaStreamSynchronize(s->stream);
+  cudaMemPoolDestroy(s->pool);
   cudaStreamDestroy(s->stream);
   cudaFree(s->d_slots);
   cudaFreeHost(s->h_slots);

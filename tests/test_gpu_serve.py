@@ -111,7 +111,7 @@ def test_oversize_request_is_refused(pip):
 def test_late_arrivals_overlap_running_requests(pip):
     """Continuous batching: a request submitted while a long one runs is
     admitted and finishes before the long one does."""
-    with pip.Server(8 << 30, rounds_per_tick=32) as srv:
+    with pip.Server(8 << 30, rounds_per_tick=32, lanes=pip.SERVE_NO_LANES) as srv:
         long_t = srv.submit(1 << 26, "u64", seed=1, eps=0.5)
         time.sleep(0.05)
         short_t = srv.submit(1 << 12, "u32", seed=2, eps=0.5)
@@ -124,7 +124,7 @@ def test_late_arrivals_overlap_running_requests(pip):
 
 
 def test_next_done_returns_completion_order(pip):
-    with pip.Server(8 << 30) as srv:
+    with pip.Server(8 << 30, lanes=pip.SERVE_NO_LANES) as srv:
         big = srv.submit(1 << 24, "u64", seed=1, eps=0.5)
         smalls = [srv.submit(1000 + k, "u32", seed=k, eps=0.5) for k in range(20)]
         got = [srv.next_done() for _ in range(21)]
@@ -133,3 +133,70 @@ def test_next_done_returns_completion_order(pip):
         for t in got:
             srv.release(t)
         assert srv.next_done(timeout_ms=10) is None
+
+
+# ------------------------------------------------------------------ lanes
+def test_lane_requests_equal_the_oracle_alone_and_in_the_mix(pip):
+    """Large requests run on lanes (the grid driver on a slice of the GPU,
+    next to the ticks); each result equals the oracle, the same request
+    served without lanes, and pip_shuffle."""
+    big = [((1 << 22) + 17, "u64", 5), ((1 << 23) + 3, "u32", 6), ((1 << 22) + 1, "rec128", 7)]
+    small = [(int(2 ** (8 + k % 12)), ["u32", "u64"][k % 2], 100 + k) for k in range(40)]
+    results = {}
+    for lanes in (0, pip.SERVE_NO_LANES):  # 0 = default lanes
+        with pip.Server(16 << 30, lanes=lanes) as srv:
+            tickets = {}
+            for j, (n, d, sd) in enumerate(big + small):
+                tickets[j] = srv.submit(n, d, seed=sd, eps=0.5)
+            for j, (n, d, sd) in enumerate(big + small):
+                ptr, st = srv.wait(tickets[j])
+                assert st.status == 0
+                results.setdefault(j, []).append(result(pip, ptr, n, d).copy())
+                srv.release(tickets[j])
+            info = srv.info()
+            assert info.status == 0 and info.used_bytes == 0
+            assert (info.lane_requests == len(big)) if lanes == 0 else (info.lane_requests == 0)
+    for j, (n, d, sd) in enumerate(big + small):
+        a, b = results[j]
+        assert np.array_equal(a, b), (n, d)
+        assert np.array_equal(a, expected(n, d, sd)), (n, d)
+    # alone: one lane request on an idle server
+    n, d, sd = big[0]
+    with pip.Server(16 << 30) as srv:
+        t = srv.submit(n, d, seed=sd, eps=0.5)
+        ptr, st = srv.wait(t)
+        assert np.array_equal(result(pip, ptr, n, d), results[0][0])
+        assert st.attempts == (n - 1) + st.losers
+
+
+def test_lane_request_is_much_faster_than_one_block(pip):
+    n = 1 << 26
+    times = {}
+    for lanes in (0, pip.SERVE_NO_LANES):
+        with pip.Server(8 << 30, lanes=lanes) as srv:
+            t = srv.submit(n, "u64", seed=3, eps=0.5)
+            ptr, st = srv.wait(t)
+            assert st.status == 0
+            times[lanes] = (st.done_ns - st.admit_ns) / 1e6
+            out = result(pip, ptr, n, "u64")
+            srv.release(t)
+    assert times[0] * 4 < times[pip.SERVE_NO_LANES], times
+    assert np.array_equal(out, expected(n, "u64", 3))
+
+
+def test_small_requests_pass_a_large_one_waiting_for_a_lane(pip):
+    """With one lane, a second large request waits for it while small
+    requests behind it are admitted to tick blocks and finish first."""
+    with pip.Server(16 << 30, lanes=1) as srv:
+        a = srv.submit(1 << 26, "u64", seed=1, eps=0.5)
+        b = srv.submit(1 << 26, "u64", seed=2, eps=0.5)
+        smalls = [srv.submit(4096 + k, "u32", seed=k, eps=0.5) for k in range(8)]
+        _, sb = srv.wait(b)
+        for k, t in enumerate(smalls):
+            ptr, st = srv.wait(t)
+            assert st.done_ns < sb.done_ns
+            assert np.array_equal(result(pip, ptr, 4096 + k, "u32"), expected(4096 + k, "u32", k))
+        _, sa = srv.wait(a)
+        assert sa.done_ns <= sb.admit_ns + 1_000_000  # b took the lane once a had left it
+        for t, sd in ((a, 1), (b, 2)):
+            assert np.array_equal(result(pip, srv.poll(t)[0], 1 << 26, "u64"), expected(1 << 26, "u64", sd))
