@@ -998,7 +998,7 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--eps", type=float, default=0.25)
     ap.add_argument("--sweep", default="0.5,0.75", help="extra eps values timed (1 step each); '' to skip")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-sample", type=int, default=1 << 27, help="elements in the oracle's timed sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prefix-c", type=float, default=0.0)

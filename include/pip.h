@@ -142,12 +142,6 @@ typedef struct {
  * checked, as the contraction reads it (an error then leaves the records
  * unspecified); the full check costs two random reads per node. */
 #define PIP_FLAG_VALIDATE_INPUT 1024u
-/* Grid driver: launch with an L2 access-policy window that marks the
- * reservation tables persisting, so that the array's random traffic does not
- * evict them.  Sets the context's persisting-L2 limit (cudaLimitPersistingL2CacheSize)
- * to the tables' size, capped by the device's maximum, and leaves it set.
- * Performance only; results are identical. */
-#define PIP_FLAG_L2_PERSIST_TABLES 2048u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {

@@ -197,7 +197,6 @@ FLAG_FORCE_CLUSTER = 128
 FLAG_SPECULATE = 256
 FLAG_TWO_RES = 512
 FLAG_VALIDATE_INPUT = 1024
-FLAG_L2_PERSIST_TABLES = 2048
 
 _lock = threading.Lock()
 _lib = None
