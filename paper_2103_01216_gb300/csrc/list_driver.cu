@@ -642,13 +642,30 @@ ListArgs list_args(const ListPlan& plan, void* rec, void* aux, pip_stats* stats)
 pip_status launch_rounds(const void* kernel, const ListPlan& plan, ListArgs a, cudaStream_t stream) {
   DeviceInfo di;
   if (device_info(&di) != PIP_OK) return PIP_ECUDA;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)plan.threads, (size_t)plan.block_smem()) !=
-          cudaSuccess ||
-      per_sm < 1) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return PIP_ECUDA;
   }
+  // occupancy of each kernel and shape, looked up once per device
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, uint32_t, uint64_t>, int> cache;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, kernel, plan.threads, plan.block_smem());
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)plan.threads,
+                                                        (size_t)plan.block_smem()) != cudaSuccess) {
+        cudaGetLastError();
+        return PIP_ECUDA;
+      }
+      it = cache.emplace(key, per_sm).first;
+    }
+    per_sm = it->second;
+  }
+  if (per_sm < 1) return PIP_ECUDA;
   const uint32_t blocks = std::max(1u, std::min<uint32_t>({plan.blocks, (uint32_t)per_sm * (uint32_t)di.sms, 1023u}));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);

@@ -245,3 +245,15 @@ def test_noalloc_refuses_host_memory_before_any_launch(pip):
     assert L.pip_shuffle_noalloc(ctypes.c_void_p(a.data_ptr()), 64, pip.DTYPES["u64"], 1, 1.5, None) == pip.PIP_EINVAL
     assert L.pip_shuffle_noalloc(ctypes.c_void_p(a.data_ptr()), 1, pip.DTYPES["u64"], 1, 0.5, None) == pip.PIP_OK
     assert torch.equal(a, torch.arange(64, dtype=torch.int64))
+
+
+def test_planner_takes_slot_factor_3_for_bound_limited_small_prefixes(pip):
+    # a small, bound-limited prefix (n = 10^9, eps = 0.5): three slots per
+    # fresh swap leave room for a larger prefix than four; an explicit slot
+    # factor is kept as given
+    p = pip.plan(10**9, "u64", 0.5)
+    p4 = pip.plan(10**9, "u64", 0.5, slot_factor=4)
+    assert p["slots"] == 3 * p["fresh_per_round"] + 32
+    assert p4["slots"] == 4 * p4["fresh_per_round"] + 32
+    assert p["fresh_per_round"] > p4["fresh_per_round"]
+    assert p["aux_bytes"] + p["smem_bytes"] <= p["aux_bound_bytes"]
