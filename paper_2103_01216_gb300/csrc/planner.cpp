@@ -205,11 +205,14 @@ pip_status make_plan_sigma(uint64_t n, pip_dtype dtype, double eps, const pip_op
   uint64_t F = (uint64_t)std::max(1.0, std::ceil(want));
   F = std::min<uint64_t>(F, n - 1);
   // the three slot tables (read, reserved into, being cleared) stay within
-  // half of L2 unless the caller fixed F explicitly
+  // a quarter of L2 unless the caller fixed F explicitly: the array's random
+  // traffic shares L2 with them (n = 10^9 u64, eps = 0.25, slot factor 4:
+  // F = 600K / 700K / 900K / 1.0M / 1.13M measured 59.2-59.5 / 59.2 / 59.7 /
+  // 60.6 / 61.5 ms on one box; 2/5 of L2 gave the 1.13M)
   DeviceInfo di;
   const bool have_dev = device_info(&di) == PIP_OK;
   if (!o.fresh_per_round && !(o.prefix_c > 0.0) && have_dev && di.l2_bytes > 0) {
-    const uint64_t hot_cap = di.l2_bytes * 2 / 5;
+    const uint64_t hot_cap = di.l2_bytes / 4;
     const uint64_t per_F = 3ull * 4ull * slot_factor;  // 3 slot tables * 4 B * slots per F
     F = std::max<uint64_t>(1, std::min<uint64_t>(F, hot_cap / per_F));
   }
