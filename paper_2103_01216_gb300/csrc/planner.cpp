@@ -342,7 +342,16 @@ pip_status make_plan_sigma(uint64_t n, pip_dtype dtype, double eps, const pip_op
   for (;;) {
     const uint64_t active_est = (uint64_t)p.F + p.F / 4 + 1;
     uint64_t want = (active_est + (uint64_t)threads * kItemsPerThread - 1) / ((uint64_t)threads * kItemsPerThread);
-    if (have_dev) want = std::max<uint64_t>(want, std::min<uint64_t>(2ull * di.sms, (active_est + 31) / 32));
+    // at least two blocks per SM while each still gets a warp's worth of
+    // items, and at most two: a third block per SM measured slower with the
+    // exchange commit (n = 10^9 u64, eps = 0.25, F = 706K: 304 blocks of 512
+    // threads 58.8 ms, 456 of 512 61.1 ms, 608 of 256 59.5 ms, 152 of 512
+    // 64.0 ms), its barrier arrivals and L2 traffic costing more than its
+    // extra memory parallelism brings
+    if (have_dev) {
+      want = std::max<uint64_t>(want, std::min<uint64_t>(2ull * di.sms, (active_est + 31) / 32));
+      want = std::min<uint64_t>(want, 2ull * di.sms);
+    }
     if (o.grid_blocks) want = o.grid_blocks;
     want = std::max<uint64_t>(1, std::min<uint64_t>(want, kGridMaxBlocks));
     // blocks that fit with the largest list first, then the list for them
