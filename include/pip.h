@@ -142,6 +142,14 @@ typedef struct {
  * checked, as the contraction reads it (an error then leaves the records
  * unspecified); the full check costs two random reads per node. */
 #define PIP_FLAG_VALIDATE_INPUT 1024u
+/* Test hook: run the grid driver the way a serving lane does -- launched
+ * without the cooperative attribute, its blocks first meeting at a start
+ * gate that gives up after wait_timeout_ns -- with errors reported in the
+ * stats record (status) rather than the per-device latch.  With
+ * PIP_FLAG_TEST_SKIP_BARRIER as well, block 0 never checks in, so the gate
+ * gives up: every block leaves before touching the array or the tables and
+ * the stats record PIP_EBUSY. */
+#define PIP_FLAG_TEST_GATED 8192u
 
 /* Per-call statistics written by the device at the end of a shuffle. */
 typedef struct {

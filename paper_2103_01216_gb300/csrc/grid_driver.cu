@@ -142,9 +142,10 @@ __device__ __forceinline__ void reserve_fresh(const GridArgs& a, uint32_t lo, ui
 // first check in.  The first block that sees every arrival, or runs out of
 // time, decides for all (compare-and-swap on one word); on an abort every
 // block leaves before touching the array or the tables, and the run reports
-// PIP_EBUSY.  Returns true when the blocks may go on.
-__device__ __noinline__ bool start_gate(Ctrl* ctrl, uint64_t timeout_ns) {
-  atomicAdd(&ctrl->gate_count, 1u);
+// PIP_EBUSY.  Returns true when the blocks may go on.  `arrive == false`
+// (a test hook) keeps this block from checking in, so the gate gives up.
+__device__ __noinline__ bool start_gate(Ctrl* ctrl, uint64_t timeout_ns, bool arrive) {
+  if (arrive) atomicAdd(&ctrl->gate_count, 1u);
   uint64_t t0 = 0;
   uint32_t polls = 0, d;
   while ((d = ld_relaxed_u32(&ctrl->gate_decision)) == 0u) {
@@ -220,7 +221,10 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
   __syncthreads();
   if (s_start_status != 0u) goto done;
   if constexpr (kGate) {
-    if (threadIdx.x == 0) s_stop = start_gate(ctrl, a.gate_timeout_ns) ? 0u : 2u;
+    if (threadIdx.x == 0)
+      s_stop = start_gate(ctrl, a.gate_timeout_ns, !((a.flags & PIP_FLAG_TEST_SKIP_BARRIER) && blockIdx.x == 0))
+                   ? 0u
+                   : 2u;
     __syncthreads();
     if (s_stop != 0u) goto done;
   }

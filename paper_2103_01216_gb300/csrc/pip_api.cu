@@ -93,6 +93,8 @@ pip_status pip_shuffle_ex(void* A_dev, uint64_t n, pip_dtype dtype, uint64_t see
   }
   if (plan.driver == kDriverCta) st = launch_cta_single(plan, A_dev, H_dev, seed, aux, stats_dev, s);
   else if (plan.driver == kDriverCluster) st = launch_cluster_driver(plan, A_dev, H_dev, seed, aux, stats_dev, s);
+  else if ((plan.flags & PIP_FLAG_TEST_GATED) && H_dev == nullptr)
+    st = launch_grid_lane(plan, A_dev, seed, aux, stats_dev, plan.timeout_ns, s);
   else st = launch_grid_driver(plan, A_dev, H_dev, seed, aux, stats_dev, s);
   if (owned && cudaFreeAsync(aux, s) != cudaSuccess && st == PIP_OK) st = PIP_ECUDA;
   return st;

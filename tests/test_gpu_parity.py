@@ -286,6 +286,41 @@ def test_barrier_wait_runs_out_and_reports_timeout(pip):
     assert np.array_equal(out, expect_hashed(arr, 1))
 
 
+@pytest.mark.parametrize("dtype", ["u32", "u64", "rec128"])
+def test_gated_launch_equals_the_oracle(pip, dtype):
+    # the grid driver as a serving lane runs it: no cooperative attribute,
+    # the blocks meet at a start gate first; alone on the GPU they all
+    # check in, and the result is the oracle's
+    n = (1 << 20) + 3
+    arr = workloads.make(n, dtype)
+    for F in (4096, 200000):  # both commit modes
+        out, stats = gpu_shuffle(pip, arr, seed=6, eps=0.5, fresh_per_round=F, with_stats=True,
+                                 flags=pip.FLAG_TEST_GATED | pip.FLAG_FORCE_GRID)
+        assert stats.status == 0
+        assert np.array_equal(out, expect_hashed(arr, 6))
+
+
+def test_start_gate_gives_up_before_touching_anything(pip):
+    """A block that never checks in makes the start gate give up: every block
+    leaves before touching the array or the tables, the run reports
+    PIP_EBUSY in its own stats, and the per-device latch stays clear."""
+    torch = torch_cuda()
+    from tests.gpu_util import to_dev, from_dev
+
+    n = 1 << 18
+    arr = workloads.iota(n, "u64")
+    A = to_dev(arr)
+    st = torch.zeros(pip.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    pip.shuffle(A, seed=1, eps=0.5, grid_blocks=8, stats=st,
+                flags=pip.FLAG_TEST_GATED | pip.FLAG_TEST_SKIP_BARRIER | pip.FLAG_FORCE_GRID,
+                wait_timeout_ns=50_000_000)
+    pip.check()  # the gate's verdict is the run's own, not the device's
+    assert pip.read_stats(st).status == pip.PIP_EBUSY
+    assert np.array_equal(from_dev(A, arr), arr)
+    out, _ = gpu_shuffle(pip, arr, seed=1, eps=0.5)
+    assert np.array_equal(out, expect_hashed(arr, 1))
+
+
 def test_caller_provided_scratch(pip):
     torch = torch_cuda()
     from tests.gpu_util import to_dev, from_dev
