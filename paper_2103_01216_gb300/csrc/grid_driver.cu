@@ -70,14 +70,17 @@ __device__ uint32_t g_error_latch;
 namespace {
 
 // Positions per thread in flight in the commit phase, and the launch bounds:
-// two positions per thread with 40 registers (three 512-thread blocks per SM)
-// measured best on GB300; at 32 registers the same loop spills, and one
-// position per thread at four blocks per SM is 2-8 % slower.
+// two positions per thread, with registers for two 512-thread blocks per SM
+// (64, no spills; the planner launches at most two blocks per SM), measured
+// best on GB300: against a bound of three blocks per SM (40 registers, a few
+// spills) 58.4 against 58.8 ms at n = 10^9 u64, eps = 0.25, 101.5 against
+// 103.9 ms at eps = 0.5 and 112.4 against 117.4 ms for 2^30 16-byte records.
+// One position per thread at four blocks per SM was 2-8 % slower.
 #ifndef PIP_KU
 #define PIP_KU 2
 #endif
 #ifndef PIP_MIN_BLOCKS
-#define PIP_MIN_BLOCKS 3
+#define PIP_MIN_BLOCKS 2
 #endif
 #ifndef PIP_MAX_THREADS
 #define PIP_MAX_THREADS 512

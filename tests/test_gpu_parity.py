@@ -132,6 +132,24 @@ def test_random_explicit_targets(pip, n, F, driver):
     assert stats.attempts == (n - 1) + stats.losers
 
 
+# ------------------------------------------------------------------ losers under conflicts
+@pytest.mark.parametrize("name", ["zero", "prev"])
+@pytest.mark.parametrize("commit", [8, 4])
+def test_grid_losers_under_conflicts(pip, name, commit):
+    """Every fresh swap but one loses in every round, so the losers overflow
+    the blocks' on-chip lists into the queue in device memory: with all
+    targets at 0 nothing targets a loser's own location; with H[i] = i-1
+    every own location is taken."""
+    n = 50021
+    H = closed_form_targets(n)[name]
+    for F in (7, 3000):
+        arr = workloads.iota(n, "u64")
+        out, st = gpu_shuffle(pip, arr, eps=0.25, H=H, fresh_per_round=F, flags=pip.FLAG_FORCE_GRID | commit,
+                              with_stats=True)
+        assert np.array_equal(out, expect_explicit(arr, H)), F
+        assert st.rounds == n - 1 and st.attempts == (n - 1) + st.losers
+
+
 # ------------------------------------------------------------------ hashed targets
 @pytest.mark.parametrize("driver", sorted(DRIVERS))
 def test_config_2pow20_u64_seed1_eps_half(pip, driver):
