@@ -197,6 +197,7 @@ FLAG_FORCE_CLUSTER = 128
 FLAG_SPECULATE = 256
 FLAG_TWO_RES = 512
 FLAG_VALIDATE_INPUT = 1024
+FLAG_EARLY_RESERVE = 4096
 FLAG_TEST_GATED = 8192
 
 _lock = threading.Lock()

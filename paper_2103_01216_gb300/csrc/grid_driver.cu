@@ -288,6 +288,16 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
     }
 
     const bool two = (a.flags & PIP_FLAG_TWO_RES) != 0u;
+    // (b) and (c) below, issued before the commit under
+    // PIP_FLAG_EARLY_RESERVE (small prefixes): the fresh block reserves in
+    // round r+1's tables and the cleaning touches round r-1's, neither of
+    // which the commit of round r reads
+    const bool early = (a.flags & PIP_FLAG_EARLY_RESERVE) != 0u;
+    if (early) {
+      reserve_fresh<Elem, kExplicit>(a, Ln, L, Dn, Sn, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+      clear_words(a.S[b2], a.nslots, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+      clear_words(a.D[b2], window_words(a.F), blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+    }
     // ---- (a) commit round r.  Each thread takes kU slots at a time and
     // issues their loads together so that kU independent memory chains are
     // in flight per thread.
@@ -401,13 +411,16 @@ __global__ void __launch_bounds__(PIP_MAX_THREADS, PIP_MIN_BLOCKS) rounds_kernel
       }
     }
 
-    // ---- (b) fresh block of round r+1 reserves (after the commit: issued
-    // before it, these atomics and stores measured 5-8 % slower)
-    reserve_fresh<Elem, kExplicit>(a, Ln, L, Dn, Sn, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+    if (!early) {
+      // ---- (b) fresh block of round r+1 reserves (after the commit for
+      // large prefixes: issued before it, these atomics and stores measured
+      // 3-8 % slower there)
+      reserve_fresh<Elem, kExplicit>(a, Ln, L, Dn, Sn, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
 
-    // ---- (c) clean round r-1's tables (they become round r+2's)
-    clear_words(a.S[b2], a.nslots, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
-    clear_words(a.D[b2], window_words(a.F), blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+      // ---- (c) clean round r-1's tables (they become round r+2's)
+      clear_words(a.S[b2], a.nslots, blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+      clear_words(a.D[b2], window_words(a.F), blockIdx.x * NT + threadIdx.x, gridDim.x * NT);
+    }
 
     // ---- barrier B_r with this block's losers (all, and those spilled to
     // the overflow queue); thread 0 turns the sums into the next round's

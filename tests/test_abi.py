@@ -257,3 +257,14 @@ def test_planner_takes_slot_factor_3_for_bound_limited_small_prefixes(pip):
     assert p4["slots"] == 4 * p4["fresh_per_round"] + 32
     assert p["fresh_per_round"] > p4["fresh_per_round"]
     assert p["aux_bytes"] + p["smem_bytes"] <= p["aux_bound_bytes"]
+
+
+def test_planner_issues_reservations_early_for_small_prefixes(pip):
+    # bound-limited small prefixes (the latency-bound regime) reserve and clean
+    # before the commit; large prefixes after it; a caller may force it
+    E = pip.FLAG_EARLY_RESERVE
+    small = pip.plan(10**9, "u64", 0.5, flags=pip.FLAG_FORCE_GRID)
+    assert small["fresh_per_round"] <= 131072 and small["flags"] & E
+    large = pip.plan(10**9, "u64", 0.25, flags=pip.FLAG_FORCE_GRID)
+    assert large["fresh_per_round"] > 131072 and not large["flags"] & E
+    assert pip.plan(10**9, "u64", 0.25, flags=pip.FLAG_FORCE_GRID | E)["flags"] & E

@@ -29,7 +29,8 @@ def pip():
 # and the grid driver under each commit mode (the exchange at L2, and plain
 # loads and stores) whatever the prefix size
 DRIVERS = {"grid": 32, "cta": 64, "cluster": 128, "grid_tworeserve": 32 | 512, "cta_tworeserve": 64 | 512,
-           "grid_exchange": 32 | 8, "grid_loadstore": 32 | 4, "grid_tworeserve_exchange": 32 | 512 | 8}
+           "grid_exchange": 32 | 8, "grid_loadstore": 32 | 4, "grid_tworeserve_exchange": 32 | 512 | 8,
+           "grid_exchange_early": 32 | 8 | 4096}
 
 
 def expect_hashed(arr, seed):
@@ -148,6 +149,24 @@ def test_grid_losers_under_conflicts(pip, name, commit):
                               with_stats=True)
         assert np.array_equal(out, expect_explicit(arr, H)), F
         assert st.rounds == n - 1 and st.attempts == (n - 1) + st.losers
+
+
+# ------------------------------------------------------------------ phase order
+@pytest.mark.parametrize("dtype", ["u32", "u64", "rec128"])
+def test_phase_order_equal_the_oracle(pip, dtype):
+    """A prefix above the planner's 128K threshold runs with the reservations
+    and the cleaning after the commit; forced early it gives the same result."""
+    n = (1 << 21) + 5
+    F = 150000
+    fl = pip.FLAG_FORCE_GRID
+    assert not pip.plan(n, dtype, 0.2, fresh_per_round=F, flags=fl)["flags"] & pip.FLAG_EARLY_RESERVE
+    assert pip.plan(n, dtype, 0.2, fresh_per_round=4096, flags=fl)["flags"] & pip.FLAG_EARLY_RESERVE
+    arr = workloads.records(n) if dtype == "rec128" else workloads.iota(n, dtype)
+    want = expect_hashed(arr, 9)
+    for extra in (0, pip.FLAG_EARLY_RESERVE):
+        out, st = gpu_shuffle(pip, arr, seed=9, eps=0.2, fresh_per_round=F, flags=fl | extra, with_stats=True)
+        assert np.array_equal(out, want), extra
+        assert st.status == 0 and st.attempts == (n - 1) + st.losers
 
 
 # ------------------------------------------------------------------ hashed targets
