@@ -75,7 +75,9 @@ namespace {
 // best on GB300: against a bound of three blocks per SM (40 registers, a few
 // spills) 58.4 against 58.8 ms at n = 10^9 u64, eps = 0.25, 101.5 against
 // 103.9 ms at eps = 0.5 and 112.4 against 117.4 ms for 2^30 16-byte records.
-// One position per thread at four blocks per SM was 2-8 % slower.
+// Three positions per thread at the same bound measured 60.4 / 98.3 / 110.4
+// against 58.0 / 97.4 / 109.0 ms; one position per thread at four blocks per
+// SM was 2-8 % slower.
 #ifndef PIP_KU
 #define PIP_KU 2
 #endif
