@@ -351,7 +351,7 @@ def test_start_gate_gives_up_before_touching_anything(pip):
     pip.shuffle(A, seed=1, eps=0.5, grid_blocks=8, stats=st,
                 flags=pip.FLAG_TEST_GATED | pip.FLAG_TEST_SKIP_BARRIER | pip.FLAG_FORCE_GRID,
                 wait_timeout_ns=50_000_000)
-    pip.check()  # the gate's verdict is the run's own, not the device's
+    pip.check()  # the gate's decision is the run's own, not the device's
     assert pip.read_stats(st).status == pip.PIP_EBUSY
     assert np.array_equal(from_dev(A, arr), arr)
     out, _ = gpu_shuffle(pip, arr, seed=1, eps=0.5)
