@@ -1315,6 +1315,29 @@ def main():
     return 0
 
 
+def oracle_pool_baseline(jobs, what):
+    """The oracle on all host cores over a bounded sample of independent
+    arrays: one sequential Knuth shuffle (oracle/knuth.c) per array of
+    A[i] = i, the arrays spread over host threads (the C oracle runs outside
+    the GIL), largest first.  jobs: (n, dtype, seed) triples.  The arrays are
+    built before the clock starts."""
+    import concurrent.futures as cf
+
+    import oracle
+    import workloads
+
+    cores = os.cpu_count() or 1
+    jobs = sorted(jobs, key=lambda j: -j[0])
+    arrs = [(workloads.iota(n, dt), int(sd)) for n, dt, sd in jobs]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda a: oracle.knuth_hash(a[0], a[1]), arrs))
+    sec = time.perf_counter() - t0
+    total = sum(n for n, _, _ in jobs)
+    return {"value": total / sec, "unit": "elems/s", "req_s": len(jobs) / sec, "cores": cores, "kind": "oracle",
+            "sample": f"{what}: {len(jobs)} arrays, {total} elements, {sec:.1f} s on {cores} host threads"}
+
+
 def run_configs(torch, pip, args, stream):
     """The rest of the workload set, each at its stated size, in this process:
     the 2^20 shuffle (L2-resident, so L2 is flushed between timed steps), the
@@ -1367,9 +1390,27 @@ def run_configs(torch, pip, args, stream):
 
     # configuration 4: the 8192-array batch
     out["batch_8192_u32"] = batch_case(torch, pip, 8192, min(args.steps, 5), min(args.warmup, 3), 1, {})
+    if not args.no_cpu:
+        import workloads
+
+        bsz, bsd = workloads.batch_workload(count=8192)
+        out["batch_8192_u32"]["cpu_baseline"] = oracle_pool_baseline(
+            [(int(bsz[j]), "u32", int(bsd[j])) for j in range(0, 8192, 16)], "every 16th array of the batch")
     # configuration 5: the serving stream
     if args.requests > 0:
         out["serve"] = serve_case(torch, pip, args.requests, {}, min(args.requests, args.plain_requests))
+        if not args.no_cpu:
+            import workloads
+
+            ssz, sdt, ssd, _ = workloads.serve_workload(count=args.requests)
+            jobs, tot = [], 0
+            for j in range(len(ssz)):
+                if tot >= 4 * 10**8:
+                    break
+                jobs.append((int(ssz[j]), str(sdt[j]), int(ssd[j])))
+                tot += int(ssz[j])
+            out["serve"]["cpu_baseline"] = oracle_pool_baseline(
+                jobs, "the stream's first requests up to 4e8 elements")
     return out
 
 
