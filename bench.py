@@ -1308,6 +1308,7 @@ def main():
         "random_swap_floor": floor,
         "configs": configs,
         "step_ms": ms,
+        "median_ms_per_step": statistics.median(ms),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
