@@ -1117,8 +1117,8 @@ def main():
         out = torch.empty(host.shape, dtype=host.dtype, pin_memory=True)
         nbytes = host.numel() * host.element_size()
         slot = (nbytes + 255) // 256 * 256
-        buf = torch.empty(3 * slot, dtype=torch.uint8, device=device)
-        pip.shuffle_host_stream([host] * 3, [out] * 3, [seed] * 3, eps=eps, dev_buf=buf)
+        buf = torch.empty(4 * slot, dtype=torch.uint8, device=device)
+        pip.shuffle_host_stream([host] * 4, [out] * 4, [seed] * 4, eps=eps, dev_buf=buf)
         pip.check()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if dist is not None:

@@ -474,9 +474,12 @@ pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, ui
  * device, shuffled as pip_shuffle(..., seeds[j], eps) would, and copied back
  * to out_hosts[j] (which may be in_hosts[j]).  A shuffle touches its whole
  * array, so its own copies cannot overlap it; array j's copies overlap the
- * shuffles of arrays j-1 and j+1 instead (three device buffers, separate
- * streams for copies in, shuffles and copies out, ordered by events; the
- * shuffles run one at a time).
+ * shuffles of arrays j-1 and j+1 instead (device buffers used in turn,
+ * separate streams for copies in, shuffles and copies out, ordered by
+ * events; the shuffles run one at a time).  A buffer passes through copy
+ * in, shuffle and copy out before it takes its next array, so four buffers
+ * are used where there is room for them (three hold the pace only while
+ * copy in + shuffle + copy out stays under three shuffles).
  *   in_hosts, out_hosts, seeds: host arrays of length count.  The arrays
  *              are independent: an input must not be another array's output
  *              (a copy in may run before an earlier array's copy out).  The copies
@@ -484,9 +487,11 @@ pip_status pip_calibrate_swap_floor(void *A_dev, uint64_t n, pip_dtype dtype, ui
  *              (cudaHostAlloc / cudaHostRegister); pageable memory works
  *              but serialises.  The host buffers must stay valid until
  *              `stream` reaches the end of the call.
- *   dev_buf  : NULL (allocated with cudaMallocAsync on `stream` and freed
- *              the same way), or caller device memory of at least
- *              min(count, 3) * round_up(n * elem, 256) bytes, 256-byte aligned.
+ *   dev_buf  : NULL (min(count, 4) buffers allocated with cudaMallocAsync
+ *              on `stream` and freed the same way), or caller device memory
+ *              of at least min(count, 3) * round_up(n * elem, 256) bytes,
+ *              256-byte aligned, of which min(count, 4) buffers are used
+ *              when dev_bytes holds them.
  *   stream   : the caller's stream; the work starts after what is queued on
  *              it and `stream` waits for the last copy back, so pip_check(stream)
  *              reports completion and any device-side error.

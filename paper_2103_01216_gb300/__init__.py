@@ -395,7 +395,8 @@ def shuffle_host_stream(ins, outs, seeds, eps: float = 0.5, *, dev_buf=None, str
     ``stream``; pinned tensors overlap, pageable ones serialise).  All tensors
     have the same shape and dtype (1-D 4- or 8-byte, or 2-D 16-byte rows).
     ``dev_buf``: optional CUDA uint8 tensor of at least
-    min(len, 3) * round_up(bytes, 256) bytes."""
+    min(len, 3) * round_up(bytes, 256) bytes (a fourth buffer is used when it
+    has room for one)."""
     ins, outs, seeds = list(ins), list(outs), [int(x) for x in seeds]
     if not (len(ins) == len(outs) == len(seeds)):
         raise ValueError("ins, outs and seeds must have the same length")

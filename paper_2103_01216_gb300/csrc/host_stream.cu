@@ -6,12 +6,18 @@
 // overlap their neighbours' shuffles: array j is copied in while array j-1 is
 // shuffled, and copied out while array j+1 is.  Three streams carry the work
 // -- host-to-device copies, shuffles, device-to-host copies -- ordered by
-// events, over three device buffers used in turn: with two, array j+1's
-// copy in would wait for array j-1's copy out (same buffer), serialising the
-// two directions (38 + 41 ms for 8 GB each way on GB300, more than a 65 ms
-// shuffle); with three they run together (51 ms for both).  The shuffles
-// stay on one stream, so two of the persistent round kernels (each wanting
-// the whole GPU) never run at once.
+// events, over device buffers used in turn: with two, array j+1's copy in
+// would wait for array j-1's copy out (same buffer), serialising the two
+// directions (38 + 41 ms for 8 GB each way on GB300, more than a 65 ms
+// shuffle); with three they run together (51 ms for both).  A buffer still
+// goes round copy in, shuffle and copy out before it takes its next array,
+// so with B buffers no array can take less than a B-th of the three stages
+// in a row: with three, a box whose copies slow to ~70 ms under a shuffle's
+// traffic is held to (61 + 70 + 70) / 3 ms per array, above the shuffle.
+// Four buffers are used where there is room for them (always when the
+// library allocates them), three at least.  The shuffles stay on one stream,
+// so two of the persistent round kernels (each wanting the whole GPU) never
+// run at once.
 #include <cstdint>
 
 #include "internal.h"
@@ -22,7 +28,7 @@ namespace {
 struct StreamSet {
   cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
   cudaEvent_t ready = nullptr;
-  static constexpr int kBufs = 3;
+  static constexpr int kBufs = 4;   // at most; kMinBufs suffice
   cudaEvent_t in_done[kBufs] = {}, shuf_done[kBufs] = {}, out_done[kBufs] = {};
 
   pip_status create() {
@@ -67,7 +73,10 @@ pip_status pip_shuffle_host_stream(const void* const* in_hosts, void* const* out
   if (n == 0) return PIP_OK;
   const uint64_t bytes = n * eb;
   const uint64_t slot = (bytes + 255) / 256 * 256;  // each buffer 256-byte aligned
-  const uint32_t nbuf = count < (uint32_t)StreamSet::kBufs ? count : (uint32_t)StreamSet::kBufs;
+  constexpr uint32_t kMinBufs = 3;
+  // buffers: one per array up to four; a caller's area gives as many as it
+  // holds, and must hold min(count, 3)
+  uint32_t nbuf = count < (uint32_t)StreamSet::kBufs ? count : (uint32_t)StreamSet::kBufs;
   cudaStream_t user = static_cast<cudaStream_t>(stream);
 
   // the scratch of one shuffle, reused by every shuffle (they are serial)
@@ -84,7 +93,9 @@ pip_status pip_shuffle_host_stream(const void* const* in_hosts, void* const* out
   void* aux = nullptr;
   bool own_buf = false;
   if (buf != nullptr) {
-    if (dev_bytes < nbuf * slot || reinterpret_cast<uintptr_t>(buf) % 256 != 0) return PIP_EINVAL;
+    const uint32_t need = nbuf < kMinBufs ? nbuf : kMinBufs;
+    if (dev_bytes < need * slot || reinterpret_cast<uintptr_t>(buf) % 256 != 0) return PIP_EINVAL;
+    if (dev_bytes / slot < nbuf) nbuf = (uint32_t)(dev_bytes / slot);
   } else {
     if (cudaMallocAsync(reinterpret_cast<void**>(&buf), nbuf * slot, user) != cudaSuccess) {
       cudaGetLastError();

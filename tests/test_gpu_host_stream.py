@@ -73,6 +73,15 @@ def test_single_array_and_caller_buffer(pip):
     pip.check()
     for j, tj in enumerate(ts):
         assert np.array_equal(to_np(tj, a), expected(a, 20 + j)), j
+    # seven arrays go round four caller buffers (room for a fourth is used),
+    # and round three when the area holds three and a half
+    for nslots in (4.0, 3.5):
+        bufx = torch.empty(int(nslots * slot), dtype=torch.uint8, device="cuda")
+        ts = [host_tensor(torch, a, True) for _ in range(7)]
+        pip.shuffle_host_stream(ts, ts, [30 + j for j in range(7)], eps=0.25, dev_buf=bufx)
+        pip.check()
+        for j, tj in enumerate(ts):
+            assert np.array_equal(to_np(tj, a), expected(a, 30 + j)), (nslots, j)
 
 
 def test_larger_arrays_many_steps(pip):
