@@ -99,7 +99,12 @@ pip_status pip_shuffle_host_stream(const void* const* in_hosts, void* const* out
   } else {
     if (cudaMallocAsync(reinterpret_cast<void**>(&buf), nbuf * slot, user) != cudaSuccess) {
       cudaGetLastError();
-      return PIP_ENOMEM;
+      // no room for the fourth buffer: three still overlap the copies
+      if (nbuf <= kMinBufs || cudaMallocAsync(reinterpret_cast<void**>(&buf), kMinBufs * slot, user) != cudaSuccess) {
+        cudaGetLastError();
+        return PIP_ENOMEM;
+      }
+      nbuf = kMinBufs;
     }
     own_buf = true;
   }
